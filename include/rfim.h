@@ -1,0 +1,159 @@
+/*
+ * rfim.h -- C ABI of librfim: Exchange Monte Carlo (parallel tempering) for the 3D Random Field
+ * Ising Model on one GB300 GPU.
+ *
+ * Paper: C. A. Navarro, W. Huang, Y. Deng, "Adaptive Multi-GPU Exchange Monte Carlo for the 3D
+ * Random Field Ising Model".  Passages implemented behind this interface:
+ *   Eq. 1      Hamiltonian H = -J sum_<ij> s_i s_j - h sum_i h_i s_i, periodic L^3 lattice.
+ *   Sec. 3.1   steps 1-4: temperature set, one field realization shared by all replicas, random
+ *              start, p Metropolis sweeps between exchanges of odd xor even adjacent pairs.
+ *   Eq. 2      exchange probability, read as W = min(1, e^Delta),
+ *              Delta = (beta_k - beta_k+1)(E(X_k) - E(X_k+1)).
+ *   Eq. 3      alternator A = (x + y + z) mod 2: colour 0 sites, then colour 1 sites.
+ *   Sec. 3.3   temperatures are swapped, not lattices ("trs"/"rts" index arrays).
+ *   Sec. 4     adaptive temperature set: midpoint insertion in the a lowest-rate intervals.
+ *   Sec. 7     Eqs. 11-12: per-temperature sums of e, e^2, |m|, m^2, m^4 (one per exchange step).
+ *
+ * Conventions
+ *   - Every function returns RFIM_OK (0) or a negative RFIM_E* code; nothing throws across the ABI.
+ *     rfim_last_error(ctx) returns the message of the last failure on that context.
+ *   - A context owns all device memory it allocates (cudaMalloc in rfim_create, freed in
+ *     rfim_destroy).  The CUDA stream in rfim_config is borrowed and must outlive the context;
+ *     NULL means the legacy default stream.  The device is the one current at rfim_create.
+ *   - Host pointers passed in are copied before the call returns.  Work is enqueued
+ *     asynchronously on the context's stream; functions that return host data synchronise it.
+ *   - A context is not thread safe; distinct contexts may be used from distinct threads.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), keyed and counted so that every flip and
+ * exchange decision is reproducible (the paper names no generator):
+ *   c3(tag, stage, colour) = (tag << 28) | (stage << 1) | colour;  tags INIT 1, METRO 2, EXCH 3, FIELD 4
+ *   field bimodal : key (field_seed, realization), ctr (i>>2, 0, 0, c3(FIELD,0,0)), word i&3, top bit 0 -> +1
+ *   field gaussian: key (field_seed, realization), ctr (i>>1, 1, 0, c3(FIELD,0,0)), words 2(i&1), 2(i&1)+1,
+ *                   Box-Muller in double, rounded to float
+ *   init          : key (seed, realization), ctr (i>>2, r, 0, c3(INIT,stage,0)), word i&3, top bit 0 -> +1
+ *   metropolis    : key (seed, realization), ctr (q>>2, r, sweep, c3(METRO,stage,colour)), word q&3,
+ *                   q = (x>>1) + (L/2)(y + L z)  (index of a site within its colour)
+ *   exchange      : key (seed, realization), ctr (k, 0, j, c3(EXCH,stage,0)), word 0
+ * Site index i = x + L (y + L z); replica index r names a lattice (it keeps its index when
+ * temperatures are exchanged); temperature index k orders the ascending temperature set.
+ */
+#ifndef RFIM_H_
+#define RFIM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RFIM_OK 0
+#define RFIM_EINVAL (-1)   /* invalid argument or configuration */
+#define RFIM_ENOMEM (-2)   /* device or host allocation failed */
+#define RFIM_ECUDA (-3)    /* a CUDA call failed (message in rfim_last_error) */
+#define RFIM_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define RFIM_EBUSY (-5)    /* result not ready yet (serving poll) */
+#define RFIM_ESTATE (-6)   /* call not valid in the current state */
+
+/* field kinds (Sec. 3.1 step 2 uses the bimodal field) */
+#define RFIM_FIELD_BIMODAL 0  /* h_i = +-1 equiprobable, drawn from field_seed */
+#define RFIM_FIELD_GAUSSIAN 1 /* h_i ~ N(0,1), drawn from field_seed */
+#define RFIM_FIELD_EXPLICIT 2 /* h_i given by the caller (float[L^3], unscaled); float arithmetic */
+
+/* spin storage layouts on the device; both give bit-identical trajectories */
+#define RFIM_LAYOUT_INT8 0    /* one byte per spin, any even L >= 2 */
+#define RFIM_LAYOUT_BITPACK 1 /* one bit per spin, L in {8, 16, 32, 64} */
+
+typedef struct rfim_ctx rfim_ctx;
+
+typedef struct {
+  int32_t L;             /* linear size, even, >= 2 (N = L^3 sites) */
+  int32_t R;             /* number of temperature replicas, >= 2 */
+  int32_t R_capacity;    /* >= R; device storage is sized for this many replicas so that the
+                            adaptive temperature set (Sec. 4) can grow without reallocation */
+  float J;               /* coupling */
+  float h;               /* field strength; hh_i = (float)h * h_i in float */
+  int32_t field_kind;    /* RFIM_FIELD_* */
+  const float *field;    /* EXPLICIT only: host float[L^3] unscaled h_i, natural site order */
+  uint32_t field_seed;   /* key word 0 of the field stream */
+  uint32_t seed;         /* key word 0 of the dynamics streams */
+  uint32_t realization;  /* key word 1 of all streams (disorder realization id) */
+  const double *temps;   /* host double[R], strictly ascending, > 0 */
+  int32_t layout;        /* RFIM_LAYOUT_* */
+  void *stream;          /* cudaStream_t (borrowed) or NULL */
+} rfim_config;
+
+/* Creates a context: copies the temperature set and (EXPLICIT) the field, generates the field
+   on the device otherwise, and draws the random start of stage 0 (Sec. 3.1 steps 1-3).
+   Errors: RFIM_EINVAL for odd L, L < 2, R < 2, R > R_capacity, non-ascending or non-positive
+   temperatures, an unknown kind/layout, a missing explicit field, or a layout that does not
+   support L; RFIM_ENOMEM if device memory runs out (nothing leaks); RFIM_ECUDA otherwise. */
+int rfim_create(const rfim_config *cfg, rfim_ctx **out);
+
+/* Frees everything the context owns (synchronising its stream first).  NULL is accepted. */
+int rfim_destroy(rfim_ctx *ctx);
+
+/* n_sweeps >= 0 full checkerboard sweeps (Eq. 3 colour 0 then colour 1) of every replica at
+   its current temperature (Sec. 3.1 step 4, Metropolis).  Asynchronous. */
+int rfim_sweep(rfim_ctx *ctx, int64_t n_sweeps);
+
+/* One exchange step j = current exchange counter (Eq. 2; pairs k = j mod 2, j mod 2 + 2, ...):
+   computes every replica's energy (Eq. 1), takes the swap decisions, permutes the temperature
+   index (Sec. 3.3), updates per-pair attempt/acceptance counts, and, when j >= measure_from,
+   adds one measurement per temperature (Sec. 7).  Asynchronous. */
+int rfim_exchange(rfim_ctx *ctx, int64_t measure_from);
+
+/* n_sweeps sweeps with an exchange step after every sweep whose 1-based global sweep count is
+   a multiple of exchange_every (exchange_every <= 0: no exchanges).  Measurements as in
+   rfim_exchange.  Asynchronous; the whole hot path runs on the device. */
+int rfim_run(rfim_ctx *ctx, int64_t n_sweeps, int32_t exchange_every, int64_t measure_from);
+
+/* Adaptive temperature set (Sec. 4).  For trial t = 1..n_trials: a fresh random start at stage t
+   with the current set, sweeps_per_trial sweeps with exchanges every exchange_every sweeps, then
+   rate_k = acc_k / att_k (0 if att_k == 0) and the midpoint temperature is inserted into each of
+   the inserts_per_trial intervals of lowest rate (min-heap order, ties to the lower k).
+   Afterwards the context is reset to stage 0 (fresh random start, identity permutation, counters
+   and accumulators zero) with the final set.  temps_out (host, capacity temps_cap) receives the
+   final set and *R_out its size.  rates_out may be NULL or host double[n_trials * R_capacity]:
+   row t-1 receives trial t's pair rates.  Synchronous.
+   Errors: RFIM_EINVAL if R + n_trials * inserts_per_trial > R_capacity, inserts_per_trial > R-1
+   at some trial, exchange_every <= 0 or temps_cap too small. */
+int rfim_adapt_temps(rfim_ctx *ctx, int32_t n_trials, int64_t sweeps_per_trial, int32_t exchange_every,
+                     int32_t inserts_per_trial, double *temps_out, int32_t temps_cap, int32_t *R_out,
+                     double *rates_out);
+
+/* Observables: caller-owned host arrays sized for R (= the context's current R); any pointer may
+   be NULL.  sums[k] are over the n_meas measurements at temperature index k (Sec. 7):
+   e = E/N, e^2, |m|, m^2, m^4 with m = M/N.  att/acc have R-1 entries (pair k, k+1).
+   Synchronous. */
+typedef struct {
+  int32_t R;        /* out: current number of replicas */
+  double *T;        /* [R] temperatures */
+  double *e, *e2, *absm, *m2, *m4; /* [R] sums */
+  uint64_t *att, *acc;             /* [R-1] */
+  int64_t n_meas;   /* out */
+} rfim_obs;
+int rfim_observables(rfim_ctx *ctx, rfim_obs *out);
+
+/* State access for tests and checkpoint/resume.  spins: host int8[R][L^3] values +-1 in natural
+   site order, indexed by replica r; t2r: int32[R] replica at temperature k; E: double[R] energy of
+   each replica recomputed from the current spins (Eq. 1); any pointer may be NULL.  Synchronous. */
+int rfim_get_state(rfim_ctx *ctx, int8_t *spins, int32_t *t2r, double *E, int64_t *sweep, int64_t *xstep);
+/* Overwrites spins (int8[R][L^3], +-1; NULL keeps them), the permutation (t2r, NULL keeps it) and
+   the sweep / exchange counters.  Accumulators and exchange statistics are left unchanged.
+   Errors: RFIM_EINVAL if t2r is not a permutation or a spin is not +-1.  Synchronous. */
+int rfim_set_state(rfim_ctx *ctx, const int8_t *spins, const int32_t *t2r, int64_t sweep, int64_t xstep);
+
+/* Copies the unscaled field h_i (float[L^3], natural order) the context uses.  Synchronous. */
+int rfim_get_field(rfim_ctx *ctx, float *h_out);
+
+/* Message of the last failed call on ctx (or of the last failed rfim_create when ctx is NULL). */
+const char *rfim_last_error(const rfim_ctx *ctx);
+
+/* Number of kernel launches this context has enqueued since creation. */
+int64_t rfim_launch_count(const rfim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFIM_H_ */

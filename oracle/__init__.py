@@ -1,0 +1,246 @@
+"""CPU oracle for the RFIM Exchange Monte Carlo hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference arm may
+import this package.  It wraps ``rfim_oracle.c`` (plain single-threaded C, no fused multiply-add)
+through ctypes and shares nothing with the CUDA path.  The C source cites the paper's sections
+and equations it follows; the random-number contract is stated in its header comment.
+
+Functions without an independent pin are listed in the repository's design notes; every
+function here is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rfim_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "librfim_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FIELD_BIMODAL = 0
+FIELD_GAUSSIAN = 1
+FIELD_EXPLICIT = 2
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with gcc (-O2, -ffp-contract=off) into oracle/_build/."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            u32, i32, i64, f32, f64 = C.c_uint32, C.c_int32, C.c_int64, C.c_float, C.c_double
+            P = C.c_void_p
+            L.orc_philox4x32_10.argtypes = [u32, u32, u32, u32, u32, u32, P]
+            L.orc_make_field.argtypes = [i32, i32, u32, u32, P]
+            L.orc_create.argtypes = [i32, i32, i32, f32, f32, i32, P, u32, u32, u32, P]
+            L.orc_create.restype = P
+            L.orc_destroy.argtypes = [P]
+            L.orc_reset.argtypes = [P, u32]
+            L.orc_sweep.argtypes = [P]
+            L.orc_exchange.argtypes = [P, i64]
+            L.orc_run.argtypes = [P, i64, i32, i64]
+            L.orc_energy.argtypes = [P, i32, P, P, P]
+            L.orc_energy.restype = f64
+            L.orc_delta_e.argtypes = [P, i32, i32, i32, i32]
+            L.orc_delta_e.restype = f64
+            L.orc_select_lowest.argtypes = [P, i32, i32, P]
+            L.orc_adapt.argtypes = [P, i32, i64, i32, i32, P]
+            L.orc_adapt.restype = i32
+            for name in ("orc_R", "orc_N"):
+                getattr(L, name).argtypes = [P]
+                getattr(L, name).restype = i32
+            for name in ("orc_sweep_count", "orc_xstep_count", "orc_n_meas"):
+                getattr(L, name).argtypes = [P]
+                getattr(L, name).restype = i64
+            L.orc_get_temps.argtypes = [P, P]
+            L.orc_get_field.argtypes = [P, P, P]
+            L.orc_get_spins.argtypes = [P, P]
+            L.orc_set_spins.argtypes = [P, P]
+            L.orc_get_perm.argtypes = [P, P, P]
+            L.orc_set_perm.argtypes = [P, P]
+            L.orc_set_counters.argtypes = [P, i64, i64]
+            L.orc_get_exchange_stats.argtypes = [P, P, P]
+            L.orc_get_energies.argtypes = [P, P, P]
+            L.orc_get_obs.argtypes = [P, P]
+            L.orc_bimodal_threshold.argtypes = [f64, f64]
+            L.orc_bimodal_threshold.restype = C.c_uint64
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def philox4x32_10(key, ctr) -> np.ndarray:
+    """Philox4x32-10 block for key (k0, k1) and counter (c0, c1, c2, c3)."""
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF,
+                            *[int(c) & 0xFFFFFFFF for c in ctr], _ptr(out))
+    return out
+
+
+def make_field(L: int, kind: int, field_seed: int, realization: int) -> np.ndarray:
+    """Unscaled field h_i (natural site order) of one realization."""
+    out = np.zeros(L ** 3, dtype=np.float32)
+    lib().orc_make_field(L, kind, field_seed, realization, _ptr(out))
+    return out
+
+
+def select_lowest(rates, a: int) -> np.ndarray:
+    r = np.ascontiguousarray(rates, dtype=np.float64)
+    out = np.zeros(max(a, 1), dtype=np.int32)
+    lib().orc_select_lowest(_ptr(r), len(r), a, _ptr(out))
+    return out[:a]
+
+
+def bimodal_threshold(beta: float, dE: float) -> int:
+    return int(lib().orc_bimodal_threshold(beta, dE))
+
+
+class Oracle:
+    """One disorder realization with R temperature replicas (see rfim_oracle.c)."""
+
+    def __init__(self, L, temps, J=1.0, h=1.0, field_kind=FIELD_GAUSSIAN, field=None,
+                 field_seed=1, seed=42, realization=0, R_capacity=None, stage=0):
+        self._lib = lib()
+        temps = np.ascontiguousarray(temps, dtype=np.float64)
+        R = len(temps)
+        Rcap = R if R_capacity is None else int(R_capacity)
+        f = None
+        if field_kind == FIELD_EXPLICIT:
+            f = np.ascontiguousarray(field, dtype=np.float32)
+            assert f.size == L ** 3
+        self._field_keep = f
+        h_ptr = _ptr(f) if f is not None else None
+        self._h = self._lib.orc_create(L, R, Rcap, J, h, field_kind, h_ptr, field_seed, seed,
+                                       realization, _ptr(temps))
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+        self.L, self.N, self.Rcap = L, L ** 3, Rcap
+        self.field_kind = field_kind
+        self._lib.orc_reset(self._h, stage)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_destroy(h)
+            self._h = None
+
+    @property
+    def R(self) -> int:
+        return self._lib.orc_R(self._h)
+
+    def reset(self, stage=0):
+        self._lib.orc_reset(self._h, stage)
+
+    def sweep(self, n=1):
+        for _ in range(n):
+            self._lib.orc_sweep(self._h)
+
+    def exchange(self, measure_from=0):
+        self._lib.orc_exchange(self._h, measure_from)
+
+    def run(self, n_sweeps, exchange_every, measure_from=0):
+        self._lib.orc_run(self._h, n_sweeps, exchange_every, measure_from)
+
+    def adapt(self, n_trials, sweeps_per_trial, exchange_every, inserts, return_rates=False):
+        rates = np.zeros((max(n_trials, 1), self.Rcap), dtype=np.float64)
+        R = self._lib.orc_adapt(self._h, n_trials, sweeps_per_trial, exchange_every, inserts,
+                                _ptr(rates))
+        if R < 0:
+            raise ValueError("invalid adaptation arguments")
+        return (R, rates[:n_trials]) if return_rates else R
+
+    def energy(self, r):
+        B = np.zeros(1, dtype=np.int64)
+        F = np.zeros(1, dtype=np.float64)
+        M = np.zeros(1, dtype=np.int64)
+        E = self._lib.orc_energy(self._h, r, _ptr(B), _ptr(F), _ptr(M))
+        return E, int(B[0]), float(F[0]), int(M[0])
+
+    def delta_e(self, r, x, y, z) -> float:
+        return self._lib.orc_delta_e(self._h, r, x, y, z)
+
+    @property
+    def sweep_count(self):
+        return self._lib.orc_sweep_count(self._h)
+
+    @property
+    def xstep_count(self):
+        return self._lib.orc_xstep_count(self._h)
+
+    @property
+    def n_meas(self):
+        return self._lib.orc_n_meas(self._h)
+
+    def temps(self):
+        T = np.zeros(self.R, dtype=np.float64)
+        self._lib.orc_get_temps(self._h, _ptr(T))
+        return T
+
+    def field(self):
+        hraw = np.zeros(self.N, dtype=np.float32)
+        hh = np.zeros(self.N, dtype=np.float32)
+        self._lib.orc_get_field(self._h, _ptr(hraw), _ptr(hh))
+        return hraw, hh
+
+    def spins(self) -> np.ndarray:
+        s = np.zeros((self.R, self.N), dtype=np.int8)
+        self._lib.orc_get_spins(self._h, _ptr(s))
+        return s
+
+    def set_spins(self, s):
+        s = np.ascontiguousarray(s, dtype=np.int8).reshape(self.R, self.N)
+        self._lib.orc_set_spins(self._h, _ptr(s))
+
+    def perm(self):
+        t2r = np.zeros(self.R, dtype=np.int32)
+        r2t = np.zeros(self.R, dtype=np.int32)
+        self._lib.orc_get_perm(self._h, _ptr(t2r), _ptr(r2t))
+        return t2r, r2t
+
+    def set_perm(self, t2r):
+        t = np.ascontiguousarray(t2r, dtype=np.int32)
+        self._lib.orc_set_perm(self._h, _ptr(t))
+
+    def set_counters(self, sweep, xstep):
+        self._lib.orc_set_counters(self._h, sweep, xstep)
+
+    def exchange_stats(self):
+        att = np.zeros(self.R - 1, dtype=np.uint64)
+        acc = np.zeros(self.R - 1, dtype=np.uint64)
+        self._lib.orc_get_exchange_stats(self._h, _ptr(att), _ptr(acc))
+        return att, acc
+
+    def energies(self):
+        E = np.zeros(self.R, dtype=np.float64)
+        M = np.zeros(self.R, dtype=np.int64)
+        self._lib.orc_get_energies(self._h, _ptr(E), _ptr(M))
+        return E, M
+
+    def observables(self):
+        obs = np.zeros((self.R, 5), dtype=np.float64)
+        self._lib.orc_get_obs(self._h, _ptr(obs))
+        return obs

@@ -1,0 +1,53 @@
+"""Brute-force references written independently of oracle/ (numpy array formulations).
+
+Used to pin the oracle: energies by periodic array shifts, exact Boltzmann averages by full
+enumeration of tiny lattices, closed forms of limiting cases.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def scaled_field(h: float, hraw: np.ndarray) -> np.ndarray:
+    """hh_i = (float)h * h_i rounded to float32, as the model's field term uses it."""
+    return (np.float32(h) * np.asarray(hraw, dtype=np.float32)).astype(np.float32)
+
+
+def energy(spins: np.ndarray, L: int, J: float, hh: np.ndarray) -> float:
+    """Eq. 1 for one configuration: -J sum over the 3N forward bonds - sum hh_i s_i."""
+    s = np.asarray(spins, dtype=np.int64).reshape(L, L, L)  # [z][y][x]
+    bonds = s * (np.roll(s, -1, axis=2) + np.roll(s, -1, axis=1) + np.roll(s, -1, axis=0))
+    field = np.sum(np.asarray(hh, dtype=np.float64).reshape(L, L, L) * s)
+    return -float(J) * float(bonds.sum()) - float(field)
+
+
+def all_states(N: int) -> np.ndarray:
+    """All 2^N configurations as int8[2^N][N] of +-1 (bit b of the state index -> site b)."""
+    idx = np.arange(2 ** N)[:, None]
+    bits = (idx >> np.arange(N)[None, :]) & 1
+    return np.where(bits == 1, 1, -1).astype(np.int8)
+
+
+def exact_averages(L: int, J: float, hh: np.ndarray, beta: float):
+    """Exact Boltzmann averages of e = E/N, e^2, |m|, m^2, m^4 by enumeration (N <= 16)."""
+    N = L ** 3
+    states = all_states(N)
+    E = np.array([energy(s, L, J, hh) for s in states])
+    M = states.astype(np.float64).sum(axis=1)
+    w = np.exp(-beta * (E - E.min()))
+    w /= w.sum()
+    e, m = E / N, M / N
+    return np.array([np.dot(w, e), np.dot(w, e * e), np.dot(w, np.abs(m)), np.dot(w, m * m),
+                     np.dot(w, m ** 4)])
+
+
+def colour_of(L: int) -> np.ndarray:
+    """Eq. 3 alternator A = (x + y + z) mod 2 for every site in natural order."""
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    return ((x + y + z) % 2).reshape(-1)
+
+
+def permutations_of(R: int):
+    return [tuple(p) for p in itertools.permutations(range(R))]
