@@ -1,0 +1,280 @@
+"""Benchmark: spin-flip attempts/ns of the Exchange Monte Carlo hot path at L = 64.
+
+Workload (one step): one disorder realization, L = 64 periodic lattice (262144 sites), Gaussian
+field h_i ~ N(0,1) with h = 1, J = 1, R = 128 temperatures geometric in [1, 5], 10^4 checkerboard
+sweeps with an exchange step every 10 sweeps (1000 exchange steps with energy reduction, swap
+decisions, temperature permutation and per-temperature measurement) -- every step of the hot path
+runs on the GPU.  Steps continue the same Markov chain.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--layout bitpack|int8]
+
+Under torchrun each rank runs its own realization (realization id = rank; weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L, R, T_MIN, T_MAX, H, J = 64, 128, 1.0, 5.0, 1.0, 1.0
+SWEEPS, EX = 10_000, 10
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Philox4x32-10 needs 20 32x32->64 multiplies per block of 4 attempts; the IMAD.WIDE pipe issues
+# 32 of them per SM per clock on GB300 (measured), which bounds the sweep at 6.4 attempts/clk/SM.
+MULWIDE_PER_CLK_SM = 32.0
+MULWIDE_PER_ATTEMPT = 5.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--layout", default="bitpack", choices=["bitpack", "int8"])
+    p.add_argument("--sweeps", type=int, default=SWEEPS)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def temps():
+    from paper_1508_06268_gb300 import inputs
+    return inputs.geometric_temps(T_MIN, T_MAX, R)
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle as it stands (single thread) on a bounded sample of the same workload."""
+    import oracle
+    T = temps()
+    o = oracle.Oracle(L, T, J=J, h=H, field_kind=oracle.FIELD_GAUSSIAN, field_seed=1, seed=42)
+    t0 = time.perf_counter()
+    o.run(1, 0, 0)
+    one = time.perf_counter() - t0
+    n = max(1, min(30, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.run(n, EX, 0)
+    dt = time.perf_counter() - t0
+    att = L ** 3 * R * n
+    return {"value": att / (dt * 1e9), "unit": "attempts/ns", "cores": 1, "kind": "oracle",
+            "sample": f"L=64 Gaussian R=128, {n} sweeps (exchange every {EX}) of the 10^4-sweep workload, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    T = temps()
+    o = oracle.Oracle(L, T, J=J, h=H, field_kind=oracle.FIELD_GAUSSIAN, field_seed=1, seed=42)
+    per_step = 2
+    for _ in range(args.warmup):
+        o.run(per_step, EX, 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.run(per_step, EX, 0)
+    dt = time.perf_counter() - t0
+    att = L ** 3 * R * per_step * args.steps
+    value = att / (dt * 1e9)
+    line = {
+        "impl": "reference", "metric": "spin-flip attempts/ns at L=64", "value": value,
+        "unit": "attempts/ns", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64/f32 (oracle)", "data": "synthetic",
+        "config": {"workload": "C4: L=64 Gaussian h=1, R=128 geometric [1,5], exchange every 10",
+                   "sample": f"{per_step} sweeps per step"},
+        "cpu_baseline": {"value": value, "unit": "attempts/ns", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} sweeps of all 128 replicas per step"},
+        "e2e": {"value": value, "unit": "attempts/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_1508_06268_gb300 as rf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    layout = rf.LAYOUT_BITPACK if args.layout == "bitpack" else rf.LAYOUT_INT8
+    T = temps()
+    real = rank
+    g = rf.Realization(L, T, J=J, h=H, field_kind=rf.FIELD_GAUSSIAN, field_seed=1 + real, seed=42,
+                       realization=real, layout=layout)
+    stream = torch.cuda.current_stream()
+    measure_from = args.sweeps // EX // 2
+    for _ in range(max(args.warmup, 3)):
+        g.run(args.sweeps, EX, measure_from)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    launches0 = g.launch_count
+    g.profile(True)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    dev_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run(args.sweeps, EX, measure_from)
+        e1.record(stream)
+        e1.synchronize()
+        dev_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    prof = g.profile_read()
+    g.profile(False)
+    launches = g.launch_count - launches0
+    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms_max = float(t.item())
+    attempts_rank = L ** 3 * R * args.sweeps * args.steps
+    value = attempts_rank * world / (dev_ms_max * 1e6)
+
+    # dominant kernel: the sweep kernel (one launch per exchange interval)
+    sweep_launch_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
+    attempts_per_launch = L ** 3 * R * EX
+    achieved = attempts_per_launch / (sweep_launch_ms * 1e6)  # Gattempts/s
+    props = torch.cuda.get_device_properties(local)
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8",
+                "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
+                              f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
+                              f"{sm_mhz:.0f} MHz (median sampled)",
+                "sweep_kernel_share": prof["sweep_ms"] / max(dev_ms, 1e-9),
+                "exchange_ms_per_step": prof["exchange_ms"] / args.steps}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(rf, torch, T, layout, args, real)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+    if rank == 0:
+        line = {
+            "metric": "spin-flip attempts/ns at L=64", "value": value, "unit": "attempts/ns",
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
+            "config": {"workload": "C4: L=64 (262144 sites) Gaussian h=1, J=1, R=128 geometric [1,5], "
+                                   f"{args.sweeps} sweeps/step, exchange every {EX}",
+                       "layout": args.layout, "l2": "flushed (512 MB write) between timed steps",
+                       "parallelism": f"realization per GPU x{world}",
+                       "wall_s": wall},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(rf, torch, T, layout, args, real):
+    """Same metric through the public API with host buffers: create from a pinned host field and
+    temperature set (H2D), run, read the observables (D2H), destroy -- all inside the timing."""
+    from paper_1508_06268_gb300 import inputs
+    field = torch.from_numpy(inputs.gaussian_field(L, 1000 + real)).pin_memory()
+    T_pin = torch.from_numpy(np.ascontiguousarray(T)).pin_memory()
+    steps = max(1, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(steps):
+        g = rf.Realization(L, T_pin.numpy(), J=J, h=H, field_kind=rf.FIELD_EXPLICIT, field=field.numpy(),
+                           seed=42, realization=real, layout=layout)
+        g.run(args.sweeps, EX, args.sweeps // EX // 2)
+        ob = g.observables()
+        d2h = sum(ob[k].nbytes for k in ("e", "e2", "absm", "m2", "m4", "att", "acc")) + 8
+        g.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": L ** 3 * R * args.sweeps * steps / (dt * 1e9), "unit": "attempts/ns",
+            "h2d_bytes_per_step": int(field.numel() * 4 + T_pin.numel() * 8), "d2h_bytes_per_step": int(d2h)}
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,21 @@ const char *rfim_last_error(const rfim_ctx *ctx);
 /* Number of kernel launches this context has enqueued since creation. */
 int64_t rfim_launch_count(const rfim_ctx *ctx);
 
+/* Kernel timing.  rfim_profile(ctx, 1) clears earlier records and starts bracketing every
+   sweep-kernel launch group (one rfim_sweep / exchange-interval worth of sweeps) and every
+   energy + exchange pair with CUDA events on the context's stream; rfim_profile(ctx, 0) stops.
+   rfim_profile_read synchronises the stream and returns the summed device time (ms) and the
+   number of bracketed groups of each kind since the last rfim_profile call.  Any output pointer
+   may be NULL. */
+int rfim_profile(rfim_ctx *ctx, int enable);
+int rfim_profile_read(rfim_ctx *ctx, double *sweep_ms, int64_t *sweep_launches, double *exchange_ms,
+                      int64_t *exchange_launches);
+
+/* Host-only self-check of the bit layout's word-level neighbour arithmetic (multi-spin coding,
+   Eq. 3 colours) against direct neighbour lookup on a random L^3 lattice; needs no GPU.
+   Returns the number of mismatching sites (0 = pass) or -1 for an unsupported L. */
+int rfim_selftest_bits(int32_t L, uint32_t seed);
+
 #ifdef __cplusplus
 }
 #endif

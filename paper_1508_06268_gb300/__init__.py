@@ -1,1 +1,217 @@
-"""GB300-native Exchange Monte Carlo for the 3D Random Field Ising Model (placeholder)."""
+"""GB300-native Exchange Monte Carlo (parallel tempering) for the 3D Random Field Ising Model.
+
+Thin ctypes binding of the C ABI in include/rfim.h (argument marshalling only: every step of the
+hot path runs in the library's CUDA kernels).  PyTorch is used for the CUDA stream handle only.
+The library is built in-tree by ``_build.build()``; when it is missing and cannot be built, every
+entry point raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ESTATE = 0, -1, -2, -3, -4, -5, -6
+FIELD_BIMODAL, FIELD_GAUSSIAN, FIELD_EXPLICIT = 0, 1, 2
+LAYOUT_INT8, LAYOUT_BITPACK = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RfimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rfim error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("L", C.c_int32), ("R", C.c_int32), ("R_capacity", C.c_int32), ("J", C.c_float),
+                ("h", C.c_float), ("field_kind", C.c_int32), ("field", C.c_void_p),
+                ("field_seed", C.c_uint32), ("seed", C.c_uint32), ("realization", C.c_uint32),
+                ("temps", C.c_void_p), ("layout", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("R", C.c_int32), ("T", C.c_void_p), ("e", C.c_void_p), ("e2", C.c_void_p),
+                ("absm", C.c_void_p), ("m2", C.c_void_p), ("m4", C.c_void_p), ("att", C.c_void_p),
+                ("acc", C.c_void_p), ("n_meas", C.c_int64)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads librfim.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("librfim.so is missing and could not be built")
+            L = C.CDLL(path)
+            P, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+            L.rfim_create.argtypes = [C.POINTER(Config), C.POINTER(C.c_void_p)]
+            L.rfim_destroy.argtypes = [P]
+            L.rfim_sweep.argtypes = [P, i64]
+            L.rfim_exchange.argtypes = [P, i64]
+            L.rfim_run.argtypes = [P, i64, i32, i64]
+            L.rfim_adapt_temps.argtypes = [P, i32, i64, i32, i32, P, i32, P, P]
+            L.rfim_observables.argtypes = [P, C.POINTER(Obs)]
+            L.rfim_get_state.argtypes = [P, P, P, P, P, P]
+            L.rfim_set_state.argtypes = [P, P, P, i64, i64]
+            L.rfim_get_field.argtypes = [P, P]
+            L.rfim_last_error.argtypes = [P]
+            L.rfim_last_error.restype = C.c_char_p
+            L.rfim_launch_count.argtypes = [P]
+            L.rfim_launch_count.restype = i64
+            L.rfim_selftest_bits.argtypes = [i32, u32]
+            L.rfim_profile.argtypes = [P, C.c_int]
+            L.rfim_profile_read.argtypes = [P, P, P, P, P]
+            for name in ("rfim_create", "rfim_destroy", "rfim_sweep", "rfim_exchange", "rfim_run",
+                         "rfim_adapt_temps", "rfim_observables", "rfim_get_state", "rfim_set_state",
+                         "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
+                         "rfim_profile_read"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _current_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def selftest_bits(L: int, seed: int = 1) -> int:
+    return load().rfim_selftest_bits(L, seed)
+
+
+class Realization:
+    """One disorder realization with R temperature replicas on the current CUDA device."""
+
+    def __init__(self, L, temps, *, R_capacity=None, J=1.0, h=1.0, field_kind=FIELD_GAUSSIAN,
+                 field=None, field_seed=1, seed=42, realization=0, layout=LAYOUT_BITPACK,
+                 stream=None):
+        self._lib = load()
+        self._h = None
+        temps = np.ascontiguousarray(temps, dtype=np.float64)
+        self._field = None if field is None else np.ascontiguousarray(field, dtype=np.float32)
+        cfg = Config()
+        cfg.L, cfg.R = L, len(temps)
+        cfg.R_capacity = len(temps) if R_capacity is None else int(R_capacity)
+        cfg.J, cfg.h, cfg.field_kind = J, h, field_kind
+        cfg.field = None if self._field is None else self._field.ctypes.data
+        cfg.field_seed, cfg.seed, cfg.realization = field_seed, seed, realization
+        cfg.temps = temps.ctypes.data
+        cfg.layout = layout
+        cfg.stream = (_current_stream() if stream is None else C.c_void_p(stream)).value
+        out = C.c_void_p()
+        rc = self._lib.rfim_create(C.byref(cfg), C.byref(out))
+        if rc != OK:
+            raise RfimError(rc, self._lib.rfim_last_error(None).decode())
+        self._h = out
+        self.L, self.N, self.R_capacity = L, L ** 3, cfg.R_capacity
+        self._R = cfg.R
+
+    def _check(self, rc):
+        if rc != OK:
+            raise RfimError(rc, self._lib.rfim_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.rfim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def R(self):
+        return self._R
+
+    def sweep(self, n=1):
+        self._check(self._lib.rfim_sweep(self._h, n))
+
+    def exchange(self, measure_from=0):
+        self._check(self._lib.rfim_exchange(self._h, measure_from))
+
+    def run(self, n_sweeps, exchange_every, measure_from=0):
+        self._check(self._lib.rfim_run(self._h, n_sweeps, exchange_every, measure_from))
+
+    def adapt_temps(self, n_trials, sweeps_per_trial, exchange_every, inserts, return_rates=False):
+        T = np.zeros(self.R_capacity, dtype=np.float64)
+        R = C.c_int32()
+        rates = np.zeros((max(n_trials, 1), self.R_capacity), dtype=np.float64)
+        self._check(self._lib.rfim_adapt_temps(self._h, n_trials, sweeps_per_trial, exchange_every,
+                                               inserts, _ptr(T), self.R_capacity, C.byref(R),
+                                               _ptr(rates)))
+        self._R = R.value
+        return (T[:self._R], rates[:n_trials]) if return_rates else T[:self._R]
+
+    def observables(self):
+        R = self._R
+        arrs = {k: np.zeros(R, dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4")}
+        att = np.zeros(max(R - 1, 1), dtype=np.uint64)
+        acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
+        o = Obs()
+        for k, a in arrs.items():
+            setattr(o, k, a.ctypes.data)
+        o.att, o.acc = att.ctypes.data, acc.ctypes.data
+        self._check(self._lib.rfim_observables(self._h, C.byref(o)))
+        arrs["att"], arrs["acc"] = att[:R - 1], acc[:R - 1]
+        arrs["n_meas"] = int(o.n_meas)
+        arrs["sums"] = np.stack([arrs[k] for k in ("e", "e2", "absm", "m2", "m4")], axis=1)
+        return arrs
+
+    def get_state(self, spins=True, t2r=True, energies=False):
+        R, N = self._R, self.N
+        s = np.zeros((R, N), dtype=np.int8) if spins else None
+        p = np.zeros(R, dtype=np.int32) if t2r else None
+        E = np.zeros(R, dtype=np.float64) if energies else None
+        sw, xs = C.c_int64(), C.c_int64()
+        self._check(self._lib.rfim_get_state(self._h, _ptr(s), _ptr(p), _ptr(E), C.byref(sw),
+                                             C.byref(xs)))
+        return {"spins": s, "t2r": p, "E": E, "sweep": sw.value, "xstep": xs.value}
+
+    def set_state(self, spins=None, t2r=None, sweep=0, xstep=0):
+        s = None if spins is None else np.ascontiguousarray(spins, dtype=np.int8)
+        p = None if t2r is None else np.ascontiguousarray(t2r, dtype=np.int32)
+        self._check(self._lib.rfim_set_state(self._h, _ptr(s), _ptr(p), sweep, xstep))
+
+    def field(self):
+        out = np.zeros(self.N, dtype=np.float32)
+        self._check(self._lib.rfim_get_field(self._h, _ptr(out)))
+        return out
+
+    def profile(self, enable=True):
+        self._check(self._lib.rfim_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        sm, sl = C.c_double(), C.c_int64()
+        em, el = C.c_double(), C.c_int64()
+        self._check(self._lib.rfim_profile_read(self._h, C.byref(sm), C.byref(sl), C.byref(em),
+                                                C.byref(el)))
+        return {"sweep_ms": sm.value, "sweep_launches": sl.value, "exchange_ms": em.value,
+                "exchange_launches": el.value}
+
+    @property
+    def launch_count(self):
+        return int(self._lib.rfim_launch_count(self._h))

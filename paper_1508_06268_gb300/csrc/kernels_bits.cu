@@ -1,0 +1,214 @@
+// Launch plan, dispatch and helpers of the bit-layout sweep kernel (kernels_bits.cuh).
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "kernels_bits.cuh"
+#include "lattice.cuh"
+#include "sweep_bits.h"
+
+namespace rfim {
+
+namespace {
+
+using KernelFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *);
+
+template <int L, int S, int GT>
+KernelFn pick(bool bim) {
+  return bim ? (KernelFn)k_sweeps_bits<L, S, GT, true> : (KernelFn)k_sweeps_bits<L, S, GT, false>;
+}
+
+KernelFn kernel_for(int L, int S, int GT, bool bim) {
+  if (L == 64) {
+    if (S == 1 && GT == 1) return pick<64, 1, 1>(bim);
+    if (S == 1 && GT == 2) return pick<64, 1, 2>(bim);
+    if (S == 2 && GT == 1) return pick<64, 2, 1>(bim);
+    if (S == 2 && GT == 2) return pick<64, 2, 2>(bim);
+    if (S == 4 && GT == 1) return pick<64, 4, 1>(bim);
+    if (S == 4 && GT == 2) return pick<64, 4, 2>(bim);
+    if (S == 4 && GT == 4) return pick<64, 4, 4>(bim);
+  } else if (L == 32) {
+    if (S == 1 && GT == 1) return pick<32, 1, 1>(bim);
+    if (S == 1 && GT == 2) return pick<32, 1, 2>(bim);
+    if (S == 2 && GT == 1) return pick<32, 2, 1>(bim);
+  } else if (L == 16) {
+    if (S == 1 && GT == 1) return pick<16, 1, 1>(bim);
+  } else if (L == 8) {
+    if (S == 1 && GT == 1) return pick<8, 1, 1>(bim);
+  }
+  return nullptr;
+}
+
+int words_per_cta(int L, int S) { return (L / S) * (L * L / 64); }
+
+__global__ void k_build_field4(RealView v, float4 *field4, int64_t wpad) {
+  const int64_t half = (int64_t)v.N / 2, W = half / 32;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * W * 8; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / (W * 8));
+    const int64_t wq = (t / 8) % W;
+    const int j = (int)(t % 8);
+    const float *h = v.hh_c + c * half + wq * 32 + 4 * j;
+    field4[field4_index(c, wq, j, wpad)] = make_float4(h[0], h[1], h[2], h[3]);
+  }
+}
+
+}  // namespace
+
+bool bits_supported(int32_t L) { return L == 8 || L == 16 || L == 32 || L == 64; }
+
+int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err) {
+  BitsPlan p;
+  p.L = L;
+  p.Rcap = Rcap;
+  if (L == 64) {
+    p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
+  } else if (L == 32) {
+    p.S = 1; p.G = 1; p.GT = 1; p.threads = 512;
+  } else if (L == 16) {
+    p.S = 1; p.G = 8; p.GT = 1; p.threads = 512;
+  } else {
+    p.S = 1; p.G = 16; p.GT = 1; p.threads = 128;
+  }
+  // "S,G,GT,threads" override (used by the launch-shape tuner and the benchmarks)
+  if (const char *o = getenv("RFIM_BITS_PLAN")) {
+    int s, g, gt, th;
+    if (sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4) {
+      p.S = s; p.G = g; p.GT = gt; p.threads = th;
+    }
+  }
+  if (p.G > Rcap) p.G = Rcap;
+  if (p.GT > p.G) p.GT = 1;
+  if (p.G % p.GT) p.G = (p.G / p.GT) * p.GT;
+  KernelFn fn = kernel_for(L, p.S, p.GT, bimodal);
+  if (!fn) {
+    if (err) *err = "no bit-layout kernel instance for this plan";
+    return -1;  // RFIM_EINVAL
+  }
+  p.smem = (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + (size_t)p.G * 128;
+  if (p.smem > 227 * 1024) {
+    if (err) *err = "bit-layout plan exceeds shared memory";
+    return -1;
+  }
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e == cudaSuccess && p.S > 1)
+    e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) {
+    if (err) *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+    return -3;  // RFIM_ECUDA
+  }
+  if (!bimodal) {
+    const int64_t W = (int64_t)L * L * L / 64, wpad = (W + 31) / 32 * 32;
+    e = cudaMalloc(&p.field4, sizeof(float4) * 2 * wpad * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (err) *err = std::string("cudaMalloc(field4): ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? -2 : -3;
+    }
+  }
+  *plan = p;
+  return 0;
+}
+
+bool bits_plan_fits(const BitsPlan &plan, int32_t R) { return R <= plan.Rcap; }
+
+void free_bits_plan(BitsPlan &plan) {
+  if (plan.field4) cudaFree(plan.field4);
+  plan.field4 = nullptr;
+}
+
+cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
+  if (!plan.field4) return cudaSuccess;
+  const int64_t W = (int64_t)v.N / 64, wpad = (W + 31) / 32 * 32;
+  k_build_field4<<<(int)((2 * W * 8 + 255) / 256), 256, 0, st>>>(v, plan.field4, wpad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
+                               cudaStream_t st) {
+  KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, v.kind == kBimodal);
+  if (!fn) return cudaErrorInvalidConfiguration;
+  const int clusters = (v.R + plan.G - 1) / plan.G;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * plan.S));
+  cfg.blockDim = dim3((unsigned)plan.threads);
+  cfg.dynamicSmemBytes = plan.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  if (plan.S > 1) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)plan.S;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, fn, v, (int32_t)plan.G, sweep0, n_sweeps, (const float4 *)plan.field4);
+}
+
+}  // namespace rfim
+
+// ---------------------------------------------------------------------------------------------
+// Host self-check of the bit-layout neighbour words against direct neighbour lookup (no GPU).
+namespace {
+
+template <int L>
+int selftest_bits_L(uint32_t seed) {
+  using namespace rfim;
+  using Gm = BitsGeom<L>;
+  const int N = L * L * L, Lh = L / 2, W = Gm::W, P = Gm::P;
+  std::vector<int> s(N);
+  uint32_t x = seed | 1u;
+  for (int i = 0; i < N; ++i) {
+    x ^= x << 13; x ^= x >> 17; x ^= x << 5;
+    s[i] = (x >> 7) & 1;
+  }
+  std::vector<uint32_t> bits(2 * W, 0u);
+  for (int i = 0; i < N; ++i) {
+    const int xx = i % L, yy = (i / L) % L, zz = i / (L * L);
+    const int c = (xx + yy + zz) & 1;
+    const int64_t q = q_of(L, Lh, xx, yy, zz);
+    bits[c * W + (q >> 5)] |= (uint32_t)s[i] << bit_of(q);
+  }
+  int bad = 0;
+  for (int c = 0; c < 2; ++c) {
+    const uint32_t *O = bits.data() + (1 - c) * W;
+    for (int wq = 0; wq < W; ++wq) {
+      const int z = wq / P, iw = wq % P;
+      uint32_t A, B, C, D;
+      nb_xy<L>(O[z * P + iw], O[z * P + (iw + 1) % P], O[z * P + (iw + P - 1) % P], parity0_mask<L>(c, z, iw), A, B, C,
+               D);
+      const uint32_t E = O[((z + 1) % L) * P + iw], F = O[((z + L - 1) % L) * P + iw];
+      uint32_t c0, c1, c2;
+      count6(A, B, C, D, E, F, c0, c1, c2);
+      for (int p = 0; p < 32; ++p) {
+        const int64_t q = (int64_t)wq * 32 + p;
+        const Site st = site_of_q(L, Lh, c, q);
+        const int b = bit_of(q);
+        auto at = [&](int xx, int yy, int zz) { return s[((zz + L) % L) * L * L + ((yy + L) % L) * L + (xx + L) % L]; };
+        const int xm = at(st.x - 1, st.y, st.z), xp = at(st.x + 1, st.y, st.z);
+        const int a = (A >> b) & 1, bb = (B >> b) & 1;
+        const bool x_ok = (a + bb == xm + xp) && ((a == xm && bb == xp) || (a == xp && bb == xm));
+        const bool y_ok = (int)((C >> b) & 1) == at(st.x, st.y + 1, st.z) && (int)((D >> b) & 1) == at(st.x, st.y - 1, st.z);
+        const bool z_ok = (int)((E >> b) & 1) == at(st.x, st.y, st.z + 1) && (int)((F >> b) & 1) == at(st.x, st.y, st.z - 1);
+        const int cnt = (int)(((c0 >> b) & 1) + 2 * ((c1 >> b) & 1) + 4 * ((c2 >> b) & 1));
+        const int ref = xm + xp + at(st.x, st.y + 1, st.z) + at(st.x, st.y - 1, st.z) + at(st.x, st.y, st.z + 1) +
+                        at(st.x, st.y, st.z - 1);
+        if (!x_ok || !y_ok || !z_ok || cnt != ref) ++bad;
+      }
+    }
+  }
+  return bad;
+}
+
+}  // namespace
+
+extern "C" int rfim_selftest_bits(int32_t L, uint32_t seed) {
+  switch (L) {
+    case 8: return selftest_bits_L<8>(seed);
+    case 16: return selftest_bits_L<16>(seed);
+    case 32: return selftest_bits_L<32>(seed);
+    case 64: return selftest_bits_L<64>(seed);
+    default: return -1;
+  }
+}

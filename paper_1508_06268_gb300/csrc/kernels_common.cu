@@ -1,0 +1,302 @@
+// Set-up, energy, exchange and conversion kernels shared by both spin layouts.
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+#include "lattice.cuh"
+#include "philox.cuh"
+
+namespace rfim {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 65535LL * 8) b = 65535LL * 8;
+  return (int)b;
+}
+
+__device__ __forceinline__ int get_spin(const RealView &v, bool bitpack, int32_t r, int32_t c, int64_t q) {
+  const int64_t half = (int64_t)v.N / 2;
+  if (bitpack) {
+    const uint32_t w = v.bits[((int64_t)r * 2 + c) * (half / 32) + (q >> 5)];
+    return (int)((w >> bit_of(q)) & 1u);
+  }
+  return v.spins8[((int64_t)r * 2 + c) * half + q];
+}
+
+// Field realization (Sec. 3.1 step 2): unscaled h_i in natural order plus the scaled,
+// colour-compacted copies the sweep kernels read.
+__global__ void k_field(RealView v, int32_t kind, uint32_t field_seed, float h, float *hraw, float *hh_c,
+                        uint8_t *hbit_c, uint32_t *hbits) {
+  const int64_t N = v.N, half = N / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    float hv;
+    if (kind == kBimodal) {
+      const Words4 w = philox10(field_seed, v.realization, (uint32_t)(i >> 2), 0u, 0u, tag_word(kTagField, 0, 0));
+      hv = (w.w[i & 3] >> 31) ? -1.0f : 1.0f;
+      hraw[i] = hv;
+    } else if (kind == kGaussian) {
+      const Words4 w = philox10(field_seed, v.realization, (uint32_t)(i >> 1), 1u, 0u, tag_word(kTagField, 0, 0));
+      const double u1 = ((double)w.w[2 * (i & 1)] + 0.5) * 0x1p-32;
+      const double u2 = ((double)w.w[2 * (i & 1) + 1] + 0.5) * 0x1p-32;
+      const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
+      hv = (float)z;
+      hraw[i] = hv;
+    } else {
+      hv = hraw[i];  // explicit: uploaded by the host
+    }
+    const int32_t L = v.L;
+    const int32_t x = (int32_t)(i % L), y = (int32_t)((i / L) % L), z = (int32_t)(i / ((int64_t)L * L));
+    const int32_t c = (x + y + z) & 1;
+    const int64_t q = q_of(L, v.Lh, x, y, z);
+    hh_c[c * half + q] = __fmul_rn(h, hv);
+    hbit_c[c * half + q] = hv > 0.0f ? 1 : 0;
+  }
+}
+
+// Bit-layout copy of the field sign bits: one thread per word.
+__global__ void k_field_bits(RealView v, const uint8_t *hbit_c, uint32_t *hbits) {
+  const int64_t half = (int64_t)v.N / 2, words = half / 32;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * words; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / words, wd = t % words;
+    uint32_t out = 0;
+    for (int p = 0; p < 32; ++p) {
+      const int64_t q = wd * 32 + p;
+      out |= (uint32_t)hbit_c[c * half + q] << bit_of(q);
+    }
+    hbits[t] = out;
+  }
+}
+
+// Random start (Sec. 3.1 step 3).
+__global__ void k_init_int8(RealView v, int32_t R, uint32_t stage) {
+  const int64_t N = v.N, half = N / 2, total = N * R;
+  const int32_t L = v.L;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(t / N);
+    const int64_t i = t % N;
+    const Words4 w = philox10(v.seed, v.realization, (uint32_t)(i >> 2), (uint32_t)r, 0u, tag_word(kTagInit, stage, 0));
+    const int32_t x = (int32_t)(i % L), y = (int32_t)((i / L) % L), z = (int32_t)(i / ((int64_t)L * L));
+    const int32_t c = (x + y + z) & 1;
+    v.spins8[((int64_t)r * 2 + c) * half + q_of(L, v.Lh, x, y, z)] = (w.w[i & 3] >> 31) ? 0 : 1;
+  }
+}
+
+// Random start in the bit layout: one thread per destination word (all 32 sites of one colour).
+__global__ void k_init_bits(RealView v, int32_t R, uint32_t stage) {
+  const int64_t half = (int64_t)v.N / 2, words = half / 32, total = (int64_t)R * 2 * words;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(t / (2 * words));
+    const int32_t c = (int32_t)((t / words) & 1);
+    const int64_t wd = t % words;
+    uint32_t out = 0;
+    for (int p = 0; p < 32; ++p) {
+      const int64_t q = wd * 32 + p;
+      const Site s = site_of_q(v.L, v.Lh, c, q);
+      const int64_t i = (int64_t)s.x + (int64_t)v.L * ((int64_t)s.y + (int64_t)v.L * s.z);
+      const Words4 w = philox10(v.seed, v.realization, (uint32_t)(i >> 2), (uint32_t)r, 0u, tag_word(kTagInit, stage, 0));
+      out |= (uint32_t)((w.w[i & 3] >> 31) ? 0u : 1u) << bit_of(q);
+    }
+    v.bits[t] = out;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Energy (Eq. 1) of every replica: B over the 3N forward bonds equals the sum over colour-0
+// sites of s_i times its six neighbours (every bond joins the two colours once; for L = 2 the
+// doubled x-pairs appear twice in both forms).  One CTA per replica.
+//   bimodal: F = h * (exact integer sum of h_i s_i), E exact in double
+//   float field: sum of hh_i s_i accumulated error-free per thread (Ogita-Rump-Oishi Sum2 in
+//   float: running sum plus the running sum of the exact TwoSum rounding errors), then in double.
+__global__ void k_energy(RealView v, double J, double h, bool bitpack) {
+  const int32_t r = blockIdx.x;
+  const int32_t L = v.L, Lh = v.Lh;
+  const int64_t half = (int64_t)v.N / 2;
+  long long B = 0, M = 0, Fi = 0;
+  float fs = 0.0f, fe = 0.0f;
+  for (int32_t c = 0; c < 2; ++c) {
+    for (int64_t q = threadIdx.x; q < half; q += blockDim.x) {
+      const int si = 2 * get_spin(v, bitpack, r, c, q) - 1;
+      M += si;
+      if (c == 0) {
+        const Site s = site_of_q(L, Lh, 0, q);
+        int64_t nq[6];
+        neighbour_qs(L, Lh, s, nq);
+        int up = 0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) up += get_spin(v, bitpack, r, 1, nq[d]);
+        B += si * (2 * up - 6);
+      }
+      if (v.kind == kBimodal) {
+        Fi += si * (v.hbit_c[c * half + q] ? 1 : -1);
+      } else {
+        const float term = si > 0 ? v.hh_c[c * half + q] : -v.hh_c[c * half + q];
+        const float t = __fadd_rn(fs, term);
+        const float bp = __fsub_rn(t, fs);
+        const float err = __fadd_rn(__fsub_rn(fs, __fsub_rn(t, bp)), __fsub_rn(term, bp));
+        fs = t;
+        fe = __fadd_rn(fe, err);
+      }
+    }
+  }
+  double F = (double)fs + (double)fe;
+  __shared__ long long sB[32], sM[32], sF[32];
+  __shared__ double sD[32];
+  B = warp_sum(B);
+  M = warp_sum(M);
+  Fi = warp_sum(Fi);
+  F = warp_sum(F);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    sB[wid] = B;
+    sM[wid] = M;
+    sF[wid] = Fi;
+    sD[wid] = F;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tb = 0, tm = 0, tf = 0;
+    double td = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      tb += sB[w];
+      tm += sM[w];
+      tf += sF[w];
+      td += sD[w];
+    }
+    const double Fv = v.kind == kBimodal ? h * (double)tf : td;
+    v.E[r] = -J * (double)tb - Fv;
+    v.M[r] = tm;
+  }
+}
+
+// One exchange step j (Eq. 2, W = min(1, e^Delta)) over the pairs k = j mod 2, j mod 2 + 2, ...,
+// swapping temperature indices (Sec. 3.3), then the Sec. 7 measurement when j >= measure_from.
+__global__ void k_exchange(RealView v, uint32_t j, int64_t measure_from) {
+  const int32_t R = v.R;
+  for (int32_t p = threadIdx.x;; p += blockDim.x) {
+    const int32_t k = (int32_t)(j & 1u) + 2 * p;
+    if (k + 1 >= R) break;
+    const int32_t a = v.t2r[k], b = v.t2r[k + 1];
+    const double delta = (v.beta_d[k] - v.beta_d[k + 1]) * (v.E[a] - v.E[b]);
+    const Words4 w = philox10(v.seed, v.realization, (uint32_t)k, 0u, j, tag_word(kTagExch, v.stage, 0));
+    const double u = (double)w.w[0] * 0x1p-32;
+    const bool accept = (delta >= 0.0) || (u < exp(delta));
+    v.att[k] += 1;
+    if (accept) {
+      v.acc[k] += 1;
+      v.t2r[k] = b;
+      v.t2r[k + 1] = a;
+      v.r2t[b] = k;
+      v.r2t[a] = k + 1;
+    }
+  }
+  __syncthreads();
+  if ((int64_t)j >= measure_from) {
+    const double Nd = (double)v.N;
+    for (int32_t k = threadIdx.x; k < R; k += blockDim.x) {
+      const int32_t a = v.t2r[k];
+      const double e = v.E[a] / Nd;
+      const double m = (double)v.M[a] / Nd;
+      double *acc = v.obs + (int64_t)k * 5;
+      acc[0] += e;
+      acc[1] += e * e;
+      acc[2] += fabs(m);
+      acc[3] += m * m;
+      acc[4] += m * m * m * m;
+    }
+    if (threadIdx.x == 0) *v.n_meas += 1;
+  }
+}
+
+__global__ void k_to_natural(RealView v, int32_t R, bool bitpack, int8_t *out) {
+  const int64_t N = v.N, total = N * R;
+  const int32_t L = v.L;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(t / N);
+    const int64_t i = t % N;
+    const int32_t x = (int32_t)(i % L), y = (int32_t)((i / L) % L), z = (int32_t)(i / ((int64_t)L * L));
+    out[t] = get_spin(v, bitpack, r, (x + y + z) & 1, q_of(L, v.Lh, x, y, z)) ? 1 : -1;
+  }
+}
+
+__global__ void k_from_natural_int8(RealView v, int32_t R, const int8_t *in) {
+  const int64_t N = v.N, half = N / 2, total = N * R;
+  const int32_t L = v.L;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(t / N);
+    const int64_t i = t % N;
+    const int32_t x = (int32_t)(i % L), y = (int32_t)((i / L) % L), z = (int32_t)(i / ((int64_t)L * L));
+    v.spins8[((int64_t)r * 2 + ((x + y + z) & 1)) * half + q_of(L, v.Lh, x, y, z)] = in[t] > 0 ? 1 : 0;
+  }
+}
+
+__global__ void k_from_natural_bits(RealView v, int32_t R, const int8_t *in) {
+  const int64_t half = (int64_t)v.N / 2, words = half / 32, total = (int64_t)R * 2 * words;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(t / (2 * words));
+    const int32_t c = (int32_t)((t / words) & 1);
+    const int64_t wd = t % words;
+    uint32_t out = 0;
+    for (int p = 0; p < 32; ++p) {
+      const int64_t q = wd * 32 + p;
+      const Site s = site_of_q(v.L, v.Lh, c, q);
+      const int64_t i = (int64_t)s.x + (int64_t)v.L * ((int64_t)s.y + (int64_t)v.L * s.z);
+      out |= (uint32_t)(in[(int64_t)r * v.N + i] > 0 ? 1u : 0u) << bit_of(q);
+    }
+    v.bits[t] = out;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_field(const RealView &v, int32_t kind, uint32_t field_seed, float h, float *hraw, float *hh_c,
+                         uint8_t *hbit_c, uint32_t *hbits, cudaStream_t st) {
+  k_field<<<grid_for(v.N, kThreads), kThreads, 0, st>>>(v, kind, field_seed, h, hraw, hh_c, hbit_c, hbits);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || hbits == nullptr) return e;
+  k_field_bits<<<grid_for(v.N / 32, kThreads), kThreads, 0, st>>>(v, hbit_c, hbits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_spins(const RealView &v, int32_t R, uint32_t stage, bool bitpack, cudaStream_t st) {
+  if (bitpack)
+    k_init_bits<<<grid_for((int64_t)R * v.N / 32, kThreads), kThreads, 0, st>>>(v, R, stage);
+  else
+    k_init_int8<<<grid_for((int64_t)R * v.N, kThreads), kThreads, 0, st>>>(v, R, stage);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st) {
+  k_energy<<<v.R, 512, 0, st>>>(v, J, h, bitpack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exchange(const RealView &v, uint32_t j, int64_t measure_from, cudaStream_t st) {
+  k_exchange<<<1, 256, 0, st>>>(v, j, measure_from);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_natural(const RealView &v, int32_t R, bool bitpack, int8_t *out, cudaStream_t st) {
+  k_to_natural<<<grid_for((int64_t)R * v.N, kThreads), kThreads, 0, st>>>(v, R, bitpack, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_natural(const RealView &v, int32_t R, bool bitpack, const int8_t *in, cudaStream_t st) {
+  if (bitpack)
+    k_from_natural_bits<<<grid_for((int64_t)R * v.N / 32, kThreads), kThreads, 0, st>>>(v, R, in);
+  else
+    k_from_natural_int8<<<grid_for((int64_t)R * v.N, kThreads), kThreads, 0, st>>>(v, R, in);
+  return cudaGetLastError();
+}
+
+}  // namespace rfim

@@ -1,0 +1,30 @@
+// Launch plan and launcher of the bit-layout sweep kernel.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rfim {
+
+// How one realization is mapped onto CTAs: a cluster of S CTAs (z slabs of L/S planes each)
+// holds G replicas; every thread updates a word of the slab for GT of them at once (so one field
+// load serves GT replicas).  Grid = ceil(R / G) clusters.
+struct BitsPlan {
+  int32_t L = 0, S = 1, G = 1, GT = 1, threads = 256;
+  size_t smem = 0;
+  int32_t Rcap = 0;
+  float4 *field4 = nullptr;  // float path: hh as float4 per (colour, word, chunk), see kernels_bits.cu
+};
+
+bool bits_supported(int32_t L);
+int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err);
+bool bits_plan_fits(const BitsPlan &plan, int32_t R);
+cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st);
+void free_bits_plan(BitsPlan &plan);
+cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
+                               cudaStream_t st);
+
+}  // namespace rfim

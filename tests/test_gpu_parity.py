@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars: bimodal field -> bit-exact spins, temperature permutation, exchange counts and measurement
+sums; Gaussian field -> flip-decision mismatch fraction <= 1e-6 by one-step replay from a shared
+state, energies to 1e-9 relative, and per-temperature <e>, <|m|> and exchange rates within 3 sigma;
+the int8 and bit layouts bit-identical to each other.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_06268_gb300 import inputs
+from tests import brute
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1508_06268_gb300 as rf  # noqa: E402
+
+BIM, GAU, EXP = rf.FIELD_BIMODAL, rf.FIELD_GAUSSIAN, rf.FIELD_EXPLICIT
+I8, BP = rf.LAYOUT_INT8, rf.LAYOUT_BITPACK
+
+
+def make_pair(L, temps, *, kind, layout, J=1.0, h=1.0, field=None, field_seed=1, seed=42,
+              realization=0, R_capacity=None):
+    g = rf.Realization(L, temps, J=J, h=h, field_kind=kind, field=field, field_seed=field_seed,
+                       seed=seed, realization=realization, layout=layout, R_capacity=R_capacity)
+    o = oracle.Oracle(L, temps, J=J, h=h, field_kind=kind, field=field, field_seed=field_seed,
+                      seed=seed, realization=realization, R_capacity=R_capacity)
+    return g, o
+
+
+def assert_same_state(g, o, what=""):
+    st = g.get_state()
+    np.testing.assert_array_equal(st["spins"], o.spins(), err_msg=f"spins {what}")
+    np.testing.assert_array_equal(st["t2r"], o.perm()[0], err_msg=f"t2r {what}")
+    assert st["sweep"] == o.sweep_count and st["xstep"] == o.xstep_count
+
+
+# ------------------------------------------------------------------ set-up steps (a1, a2, a3)
+@pytest.mark.parametrize("L", [2, 8, 16, 64])
+def test_bimodal_field_bit_exact(L):
+    g, o = make_pair(L, inputs.geometric_temps(1.0, 5.0, 2), kind=BIM, layout=I8, field_seed=5,
+                     realization=3)
+    np.testing.assert_array_equal(g.field(), o.field()[0])
+
+
+@pytest.mark.parametrize("L", [4, 32, 64])
+def test_gaussian_field_within_one_ulp(L):
+    g, o = make_pair(L, inputs.geometric_temps(1.0, 5.0, 2), kind=GAU, layout=I8, field_seed=9,
+                     realization=1)
+    a, b = g.field(), o.field()[0]
+    diff = np.abs(a.view(np.int32).astype(np.int64) - b.view(np.int32).astype(np.int64))
+    assert diff.max() <= 1
+    assert (diff == 0).mean() > 0.999
+
+
+@pytest.mark.parametrize("L,layout", [(2, I8), (6, I8), (8, I8), (8, BP), (16, BP), (64, BP)])
+def test_random_start_bit_exact(L, layout):
+    g, o = make_pair(L, inputs.geometric_temps(1.0, 5.0, 5), kind=BIM, layout=layout)
+    assert_same_state(g, o, "start")
+
+
+# ------------------------------------------------------------------ sweep + exchange (a4-a8)
+@pytest.mark.parametrize("L,R,layout,sweeps,ex", [
+    (2, 3, I8, 40, 1),        # degenerate lattice: x neighbours coincide
+    (4, 4, I8, 60, 3),
+    (6, 5, I8, 30, 5),        # L not a multiple of 8: Philox blocks straddle rows
+    (8, 16, I8, 50, 10),
+    (8, 16, BP, 50, 10),
+    (16, 32, BP, 60, 5),      # C2 shape (bimodal h = 1.5, R = 32, exchange every 5)
+    (16, 32, I8, 20, 5),
+    (32, 6, BP, 20, 10),
+    (64, 6, BP, 6, 3),        # replica count not a multiple of the cluster's replicas
+])
+def test_bimodal_trajectory_bit_exact(L, R, layout, sweeps, ex):
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    g, o = make_pair(L, temps, kind=BIM, layout=layout, h=1.5, field_seed=1, seed=42)
+    g.run(sweeps, ex, 1)
+    o.run(sweeps, ex, 1)
+    assert_same_state(g, o, f"after {sweeps} sweeps")
+    go, (att, acc) = g.observables(), o.exchange_stats()
+    np.testing.assert_array_equal(go["att"], att)
+    np.testing.assert_array_equal(go["acc"], acc)
+    assert go["n_meas"] == o.n_meas
+    np.testing.assert_array_equal(go["sums"], o.observables())  # exact energies -> exact sums
+    E = g.get_state(spins=False, t2r=False, energies=True)["E"]
+    np.testing.assert_array_equal(E, np.array([o.energy(r)[0] for r in range(R)]))
+
+
+def test_bimodal_full_size_bit_exact():
+    """L = 64, R = 128 in the launch configuration the benchmark times, a few sweeps."""
+    temps = inputs.geometric_temps(1.0, 5.0, 128)
+    g, o = make_pair(64, temps, kind=BIM, layout=BP, h=1.0, field_seed=2, seed=42)
+    g.run(4, 2, 0)
+    o.run(4, 2, 0)
+    assert_same_state(g, o, "full size")
+
+
+@pytest.mark.parametrize("L,R", [(8, 16), (16, 8), (32, 4), (64, 4)])
+def test_layouts_bit_identical(L, R):
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 100 + L)
+    outs = []
+    for layout in (I8, BP):
+        g = rf.Realization(L, temps, field_kind=EXP, field=field, layout=layout, seed=7)
+        g.run(12, 4, 0)
+        outs.append(g.get_state())
+        outs.append(g.observables())
+    np.testing.assert_array_equal(outs[0]["spins"], outs[2]["spins"])
+    np.testing.assert_array_equal(outs[0]["t2r"], outs[2]["t2r"])
+    np.testing.assert_array_equal(outs[1]["acc"], outs[3]["acc"])
+
+
+def _replay_mismatch(L, R, layout, warm=3, seed=11):
+    """One sweep from the same oracle-made state on both sides; counts differing decisions.
+    Colour-0 sites are final after the first half-sweep; colour-1 sites are compared only where
+    all six colour-0 neighbours agree (identical inputs to the decision)."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, seed)
+    o = oracle.Oracle(L, temps, field_kind=EXP, field=field, seed=42)
+    o.run(warm, 0, 0)
+    start = o.spins()
+    g = rf.Realization(L, temps, field_kind=EXP, field=field, seed=42, layout=layout)
+    g.set_state(spins=start, t2r=o.perm()[0], sweep=o.sweep_count, xstep=o.xstep_count)
+    o.sweep(1)
+    g.sweep(1)
+    a, b = g.get_state()["spins"], o.spins()
+    colour = brute.colour_of(L)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    nbr = []
+    for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+        nbr.append((((z + dz) % L) * L * L + ((y + dy) % L) * L + (x + dx) % L).reshape(-1))
+    nbr = np.stack(nbr, axis=1)
+    diff = a != b
+    mism = int(diff[:, colour == 0].sum())
+    att = int(R * (colour == 0).sum())
+    c1 = np.where(colour == 1)[0]
+    same_inputs = ~np.any(diff[:, nbr[c1]], axis=2)  # [R, n_c1]
+    mism += int((diff[:, c1] & same_inputs).sum())
+    att += int(same_inputs.sum())
+    return mism, att
+
+
+@pytest.mark.parametrize("L,R,layout", [(8, 16, BP), (16, 16, I8), (32, 8, BP), (64, 4, BP)])
+def test_gaussian_flip_decision_mismatch_fraction(L, R, layout):
+    mism, att = _replay_mismatch(L, R, layout)
+    assert att > 0
+    assert mism / att <= 1e-6 or mism <= 1, (mism, att)
+
+
+def test_gaussian_energies_match():
+    L, R = 16, 8
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 3)
+    o = oracle.Oracle(L, temps, field_kind=EXP, field=field)
+    o.run(5, 0, 0)
+    g = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP)
+    g.set_state(spins=o.spins())
+    E = g.get_state(spins=False, t2r=False, energies=True)["E"]
+    ref = np.array([o.energy(r)[0] for r in range(R)])
+    np.testing.assert_allclose(E, ref, rtol=1e-9, atol=1e-7)
+
+
+def _binned_obs(run, n_bins):
+    means, prev = [], None
+    for _ in range(n_bins):
+        s, n, acc = run()
+        if prev is not None:
+            means.append(((s - prev[0]) / (n - prev[1]), acc - prev[2]))
+        prev = (s, n, acc)
+    m = np.array([x[0] for x in means])
+    return m.mean(axis=0), m.std(axis=0, ddof=1) / math.sqrt(len(m))
+
+
+def test_gaussian_statistics_within_three_sigma():
+    """L = 8, R = 16 Gaussian (the small configuration): <e>, <|m|> per temperature."""
+    L, R, ex = 8, 16, 10
+    temps = inputs.geometric_temps(1.5, 5.0, R)
+    g, o = make_pair(L, temps, kind=GAU, layout=BP, field_seed=1, seed=42)
+    g.run(200, ex, 0)
+    o.run(200, ex, 0)
+
+    def rg():
+        g.run(100, ex, 0)
+        ob = g.observables()
+        return ob["sums"], ob["n_meas"], ob["acc"].astype(np.int64)
+
+    def ro():
+        o.run(100, ex, 0)
+        return o.observables(), o.n_meas, o.exchange_stats()[1].astype(np.int64)
+
+    mg, eg = _binned_obs(rg, 21)
+    mo, eo = _binned_obs(ro, 21)
+    sig = np.sqrt(eg ** 2 + eo ** 2) + 1e-12
+    z = np.abs(mg - mo)[:, [0, 2]] / sig[:, [0, 2]]
+    assert (z > 3).sum() <= max(2, int(0.01 * z.size)), z
+    ga, gc = g.observables()["att"], g.observables()["acc"]
+    oa, oc = o.exchange_stats()
+    rg_, ro_ = gc / ga, oc / oa
+    se = np.sqrt(rg_ * (1 - rg_) / ga + ro_ * (1 - ro_) / oa) + 1e-3
+    assert (np.abs(rg_ - ro_) / se > 3).sum() <= 2
+
+
+# ------------------------------------------------------------------ adaptation (a9)
+@pytest.mark.parametrize("layout", [I8, BP])
+def test_adaptation_bit_exact_bimodal(layout):
+    L, R0, trials, a = 8, 6, 3, 2
+    temps = inputs.geometric_temps(1.0, 5.0, R0)
+    g, o = make_pair(L, temps, kind=BIM, layout=layout, h=1.5, R_capacity=R0 + trials * a)
+    Tg, rg_ = g.adapt_temps(trials, 200, 5, a, return_rates=True)
+    Ro, ro_ = o.adapt(trials, 200, 5, a, return_rates=True)
+    assert g.R == Ro == R0 + trials * a
+    np.testing.assert_array_equal(Tg, o.temps())
+    np.testing.assert_array_equal(rg_, ro_)
+    assert_same_state(g, o, "after adaptation")
+
+
+# ------------------------------------------------------------------ boundary behaviour
+def test_invalid_configurations_rejected():
+    with pytest.raises(rf.RfimError) as e:
+        rf.Realization(7, [1.0, 2.0], layout=I8)
+    assert e.value.code == rf.EINVAL
+    with pytest.raises(rf.RfimError):
+        rf.Realization(6, [1.0, 2.0], layout=BP)
+    with pytest.raises(rf.RfimError):
+        rf.Realization(8, [2.0, 1.0])
+    with pytest.raises(rf.RfimError):
+        rf.Realization(8, [1.0])
+    g = rf.Realization(8, [1.0, 2.0, 3.0], layout=BP)
+    with pytest.raises(rf.RfimError):
+        g.set_state(t2r=np.array([0, 0, 1]))
+    with pytest.raises(rf.RfimError):
+        g.adapt_temps(1, 10, 5, 2)  # capacity 3 cannot take 2 insertions
+    g.sweep(0)
+    assert g.get_state()["sweep"] == 0
