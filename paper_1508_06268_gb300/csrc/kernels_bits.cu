@@ -12,7 +12,7 @@ namespace rfim {
 
 namespace {
 
-using KernelFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *);
+using KernelFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *, ExchArgs);
 
 template <int L, int S, int GT>
 KernelFn pick(bool bim) {
@@ -97,14 +97,31 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     if (err) *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return -3;  // RFIM_ECUDA
   }
+  auto grab = [&](void **ptr, size_t bytes, const char *what) -> int {
+    cudaError_t ee = cudaMalloc(ptr, bytes);
+    if (ee != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      if (err) *err = std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(ee);
+      return ee == cudaErrorMemoryAllocation ? -2 : -3;
+    }
+    return 0;
+  };
+  int rc = 0;
   if (!bimodal) {
     const int64_t W = (int64_t)L * L * L / 64, wpad = (W + 31) / 32 * 32;
-    e = cudaMalloc(&p.field4, sizeof(float4) * 2 * wpad * 8);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      if (err) *err = std::string("cudaMalloc(field4): ") + cudaGetErrorString(e);
-      return e == cudaErrorMemoryAllocation ? -2 : -3;
-    }
+    rc = grab((void **)&p.field4, sizeof(float4) * 2 * wpad * 8, "field4");
+  }
+  const size_t parts = (size_t)Rcap * p.S;
+  if (!rc) rc = grab((void **)&p.partB, parts * 8, "partials");
+  if (!rc) rc = grab((void **)&p.partM, parts * 8, "partials");
+  if (!rc) rc = grab((void **)&p.partFi, parts * 8, "partials");
+  if (!rc) rc = grab((void **)&p.partF, parts * 8, "partials");
+  if (!rc) rc = grab((void **)&p.counter, 4, "counter");
+  if (!rc && cudaMemset(p.counter, 0, 4) != cudaSuccess) rc = -3;
+  if (rc) {
+    free_bits_plan(p);
+    return rc;
   }
   *plan = p;
   return 0;
@@ -113,8 +130,13 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
 bool bits_plan_fits(const BitsPlan &plan, int32_t R) { return R <= plan.Rcap; }
 
 void free_bits_plan(BitsPlan &plan) {
-  if (plan.field4) cudaFree(plan.field4);
+  void *ptrs[] = {plan.field4, plan.partB, plan.partM, plan.partFi, plan.partF, plan.counter};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
   plan.field4 = nullptr;
+  plan.partB = plan.partM = plan.partFi = nullptr;
+  plan.partF = nullptr;
+  plan.counter = nullptr;
 }
 
 cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
@@ -125,7 +147,19 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
 }
 
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
+                               bool exchange, uint32_t j, int64_t measure_from, double J, double h,
                                cudaStream_t st) {
+  ExchArgs xa;
+  xa.enabled = exchange ? 1 : 0;
+  xa.j = j;
+  xa.measure_from = measure_from;
+  xa.J = J;
+  xa.h = h;
+  xa.partB = plan.partB;
+  xa.partM = plan.partM;
+  xa.partFi = plan.partFi;
+  xa.partF = plan.partF;
+  xa.counter = plan.counter;
   KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, v.kind == kBimodal);
   if (!fn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;
@@ -143,7 +177,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     cfg.attrs = at;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, fn, v, (int32_t)plan.G, sweep0, n_sweeps, (const float4 *)plan.field4);
+  return cudaLaunchKernelEx(&cfg, fn, v, (int32_t)plan.G, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
 }
 
 }  // namespace rfim

@@ -1,4 +1,5 @@
-// Bit-layout (multi-spin coded) checkerboard sweep kernel, resident in shared memory.
+// Bit-layout (multi-spin coded) checkerboard sweep kernel, resident in shared memory, with the
+// energy reduction and the exchange step fused into its tail.
 //
 // One cluster of S CTAs holds G replicas of a realization; CTA `rank` holds the z planes
 // [rank L/S, (rank + 1) L/S) of both colours of all G replicas in shared memory for the whole
@@ -8,15 +9,32 @@
 // barrier).  A thread updates one 32-site word for GT replicas: neighbour counts by bit-sliced
 // adders, then per Philox block (4 sites) one table lookup and one compare per site; the float
 // field of those 4 sites is loaded once for all GT replicas.
+//
+// Exchange tail (optional): every CTA reduces the bond sum, magnetisation and field term of its
+// slab of each of its replicas (Eq. 1) into per-slab partials; the last CTA of the grid to arrive
+// (atomic arrival counter) adds the partials in slab order, forms E = -J B - F and takes the
+// exchange step and the measurement (exchange.cuh).  No CTA waits for another.
 #pragma once
 #include <cstdint>
 
 #include "bits_layout.cuh"
 #include "decide.cuh"
+#include "exchange.cuh"
 #include "internal.h"
 #include "philox.cuh"
 
 namespace rfim {
+
+// Arguments of the fused exchange tail.  Partials are [Rcap][S]; counter is zero between launches.
+struct ExchArgs {
+  int32_t enabled;
+  uint32_t j;
+  int64_t measure_from;
+  double J, h;
+  long long *partB, *partM, *partFi;
+  double *partF;
+  unsigned int *counter;
+};
 
 __host__ __device__ __forceinline__ int64_t field4_index(int c, int64_t wq, int j, int64_t wpad) {
   return ((int64_t)c * wpad + (wq & ~31LL)) * 8 + (int64_t)j * 32 + (wq & 31);
@@ -52,9 +70,36 @@ __device__ __forceinline__ uint32_t spread(uint32_t x, int b, int j) {
   return s & (0x01010101u << b);
 }
 
+// The six other-colour neighbour words of local word (zl, iw) from plane array O (this CTA's
+// planes; halo planes from the neighbouring ranks).
+template <int L, int S>
+__device__ __forceinline__ void neighbour_words(const uint32_t *O, int zl, int iw, uint32_t p0, int up_rank,
+                                                int dn_rank, uint32_t nb[6]) {
+  constexpr int P = BitsGeom<L>::P, PZ = L / S;
+  const uint32_t same = O[zl * P + iw];
+  const uint32_t next = O[zl * P + (iw + 1) % P];
+  const uint32_t prev = O[zl * P + (iw + P - 1) % P];
+  nb_xy<L>(same, next, prev, p0, nb[0], nb[1], nb[2], nb[3]);
+  if (zl + 1 < PZ)
+    nb[4] = O[(zl + 1) * P + iw];
+  else
+    nb[4] = S == 1 ? O[iw] : dsmem_load(O + iw, up_rank);
+  if (zl > 0)
+    nb[5] = O[(zl - 1) * P + iw];
+  else
+    nb[5] = S == 1 ? O[(PZ - 1) * P + iw] : dsmem_load(O + (PZ - 1) * P + iw, dn_rank);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_reduce_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
 template <int L, int S, int GT, bool BIM>
 __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint32_t sweep0, int32_t nsw,
-                                                     const float4 *__restrict__ field4) {
+                                                     const float4 *__restrict__ field4, ExchArgs xa) {
   using Gm = BitsGeom<L>;
   constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
@@ -64,7 +109,7 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
   const int r0 = (int)(blockIdx.x / S) * G;
   const int gact = min(G, v.R - r0);
   const int z0 = rank * PZ;
-  uint32_t *sp = sm;  // [G][2][WC]
+  uint32_t *sp = sm;                        // [G][2][WC]
   uint32_t *tab = sm + (size_t)G * 2 * WC;  // BIM: [G][32] uint32; else [G][16] float2
   const int nt = blockDim.x, tid = threadIdx.x;
 
@@ -100,27 +145,19 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
         const int zl = wl / P, iw = wl % P;
         const int z = z0 + zl;
         const int64_t wq = (int64_t)z * P + iw;
+        float4 hh4[8];
+        if (!BIM) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
+        }
         const uint32_t p0 = parity0_mask<L>(c, z, iw);
         uint32_t c0[GT], c1[GT], c2[GT], sf[GT], flip[GT];
 #pragma unroll
         for (int gg = 0; gg < GT; ++gg) {
           const int g = min(grp * GT + gg, gact - 1);
-          const uint32_t *O = sp + ((size_t)g * 2 + (c ^ 1)) * WC;
-          const uint32_t same = O[zl * P + iw];
-          const uint32_t next = O[zl * P + (iw + 1) % P];
-          const uint32_t prev = O[zl * P + (iw + P - 1) % P];
-          uint32_t A, B, C, D;
-          nb_xy<L>(same, next, prev, p0, A, B, C, D);
-          uint32_t E, F;
-          if (zl + 1 < PZ)
-            E = O[(zl + 1) * P + iw];
-          else
-            E = S == 1 ? O[iw] : dsmem_load(O + iw, up_rank);
-          if (zl > 0)
-            F = O[(zl - 1) * P + iw];
-          else
-            F = S == 1 ? O[(PZ - 1) * P + iw] : dsmem_load(O + (PZ - 1) * P + iw, dn_rank);
-          count6(A, B, C, D, E, F, c0[gg], c1[gg], c2[gg]);
+          uint32_t nb[6];
+          neighbour_words<L, S>(sp + ((size_t)g * 2 + (c ^ 1)) * WC, zl, iw, p0, up_rank, dn_rank, nb);
+          count6(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], c0[gg], c1[gg], c2[gg]);
           sf[gg] = sp[((size_t)g * 2 + c) * WC + wl];
           flip[gg] = 0u;
         }
@@ -128,8 +165,6 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
         if (BIM) fb = v.hbits[(int64_t)c * W + wq];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          float4 hh4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (!BIM) hh4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
 #pragma unroll
           for (int gg = 0; gg < GT; ++gg) {
             const int g = grp * GT + gg;
@@ -143,7 +178,7 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
               acc = spread(c0[gg], 3, j) | spread(c1[gg], 4, j) | spread(c2[gg], 5, j) | spread(sf[gg], 6, j);
             }
             const char *tb = reinterpret_cast<const char *>(tab) + g * 128;
-            const float hk[4] = {hh4.x, hh4.y, hh4.z, hh4.w};
+            const float hk[4] = {hh4[j].x, hh4[j].y, hh4[j].z, hh4[j].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const uint32_t off = (acc >> (8 * k)) & 0xFFu;
@@ -173,6 +208,101 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl] = sp[t];
   }
+  if (!xa.enabled) return;
+
+  // ---- energy partials of this slab (Eq. 1): B over colour-0 words x their six neighbour words,
+  // M over all words, field term exact integer (bimodal) or error-free float sum (Sum2) -------
+  __shared__ long long red_i[3][32];
+  __shared__ double red_d[32];
+  __shared__ int last_cta;
+  const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+  for (int g = 0; g < gact; ++g) {
+    long long b = 0, m = 0, fi = 0;
+    float fs = 0.f, fe = 0.f;
+    for (int t = tid; t < 2 * WC; t += nt) {
+      const int c = t / WC, wl = t % WC;
+      const int zl = wl / P, iw = wl % P, z = z0 + zl;
+      const int64_t wq = (int64_t)z * P + iw;
+      const uint32_t self = sp[((size_t)g * 2 + c) * WC + wl];
+      m += 2 * __popc(self) - 32;
+      if (c == 0) {
+        uint32_t nb[6];
+        neighbour_words<L, S>(sp + ((size_t)g * 2 + 1) * WC, zl, iw, parity0_mask<L>(0, z, iw), up_rank, dn_rank, nb);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nb[d]);
+      }
+      if (BIM) {
+        fi += 32 - 2 * __popc(self ^ v.hbits[(int64_t)c * W + wq]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
+          const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float term = ((self >> (8 * k + j)) & 1u) ? hk[k] : -hk[k];
+            const float tsum = __fadd_rn(fs, term);
+            const float bp = __fsub_rn(tsum, fs);
+            fe = __fadd_rn(fe, __fadd_rn(__fsub_rn(fs, __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
+            fs = tsum;
+          }
+        }
+      }
+    }
+    b = warp_reduce_sum(b);
+    m = warp_reduce_sum(m);
+    fi = warp_reduce_sum(fi);
+    double fd = warp_reduce_sum((double)fs + (double)fe);
+    if (lane == 0) {
+      red_i[0][wid] = b;
+      red_i[1][wid] = m;
+      red_i[2][wid] = fi;
+      red_d[wid] = fd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long tb = 0, tm = 0, tf = 0;
+      double td = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        tb += red_i[0][w];
+        tm += red_i[1][w];
+        tf += red_i[2][w];
+        td += red_d[w];
+      }
+      const int64_t slot = (int64_t)(r0 + g) * S + rank;
+      xa.partB[slot] = tb;
+      xa.partM[slot] = tm;
+      xa.partFi[slot] = tf;
+      xa.partF[slot] = td;
+    }
+    __syncthreads();
+  }
+  sync_slabs<S>();  // peers may still read this CTA's halo planes
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(xa.counter, 1u);
+    last_cta = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_cta) return;
+  __threadfence();
+  for (int r = tid; r < v.R; r += nt) {
+    long long tb = 0, tm = 0, tf = 0;
+    double td = 0.0;
+    for (int q = 0; q < S; ++q) {
+      const int64_t slot = (int64_t)r * S + q;
+      tb += __ldcg(xa.partB + slot);
+      tm += __ldcg(xa.partM + slot);
+      tf += __ldcg(xa.partFi + slot);
+      td += __ldcg(xa.partF + slot);
+    }
+    const double F = BIM ? xa.h * (double)tf : td;
+    v.E[r] = -xa.J * (double)tb - F;
+    v.M[r] = tm;
+  }
+  __syncthreads();
+  exchange_and_measure(v, xa.j, xa.measure_from);
+  if (tid == 0) *xa.counter = 0u;
 }
 
 }  // namespace rfim

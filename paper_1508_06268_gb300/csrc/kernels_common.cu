@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "exchange.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 #include "philox.cuh"
@@ -179,44 +180,8 @@ __global__ void k_energy(RealView v, double J, double h, bool bitpack) {
   }
 }
 
-// One exchange step j (Eq. 2, W = min(1, e^Delta)) over the pairs k = j mod 2, j mod 2 + 2, ...,
-// swapping temperature indices (Sec. 3.3), then the Sec. 7 measurement when j >= measure_from.
-__global__ void k_exchange(RealView v, uint32_t j, int64_t measure_from) {
-  const int32_t R = v.R;
-  for (int32_t p = threadIdx.x;; p += blockDim.x) {
-    const int32_t k = (int32_t)(j & 1u) + 2 * p;
-    if (k + 1 >= R) break;
-    const int32_t a = v.t2r[k], b = v.t2r[k + 1];
-    const double delta = (v.beta_d[k] - v.beta_d[k + 1]) * (v.E[a] - v.E[b]);
-    const Words4 w = philox10(v.seed, v.realization, (uint32_t)k, 0u, j, tag_word(kTagExch, v.stage, 0));
-    const double u = (double)w.w[0] * 0x1p-32;
-    const bool accept = (delta >= 0.0) || (u < exp(delta));
-    v.att[k] += 1;
-    if (accept) {
-      v.acc[k] += 1;
-      v.t2r[k] = b;
-      v.t2r[k + 1] = a;
-      v.r2t[b] = k;
-      v.r2t[a] = k + 1;
-    }
-  }
-  __syncthreads();
-  if ((int64_t)j >= measure_from) {
-    const double Nd = (double)v.N;
-    for (int32_t k = threadIdx.x; k < R; k += blockDim.x) {
-      const int32_t a = v.t2r[k];
-      const double e = v.E[a] / Nd;
-      const double m = (double)v.M[a] / Nd;
-      double *acc = v.obs + (int64_t)k * 5;
-      acc[0] += e;
-      acc[1] += e * e;
-      acc[2] += fabs(m);
-      acc[3] += m * m;
-      acc[4] += m * m * m * m;
-    }
-    if (threadIdx.x == 0) *v.n_meas += 1;
-  }
-}
+// One exchange step j plus measurement (exchange.cuh), one CTA.
+__global__ void k_exchange(RealView v, uint32_t j, int64_t measure_from) { exchange_and_measure(v, j, measure_from); }
 
 __global__ void k_to_natural(RealView v, int32_t R, bool bitpack, int8_t *out) {
   const int64_t N = v.N, total = N * R;

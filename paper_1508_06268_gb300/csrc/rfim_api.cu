@@ -221,7 +221,8 @@ int do_sweeps(rfim_ctx *c, int64_t n) {
   cudaEvent_t stop;
   CUDA_OR_FAIL(c, prof_begin(c, 0, &stop));
   if (c->layout == RFIM_LAYOUT_BITPACK) {
-    CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, c->stream));
+    CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, false, 0u, 0, (double)c->J,
+                                       (double)c->h, c->stream));
     c->launches += 1;
     c->sweep += n;
   } else {
@@ -237,7 +238,22 @@ int do_sweeps(rfim_ctx *c, int64_t n) {
   return RFIM_OK;
 }
 
+// Bit layout: n sweeps and the exchange step in one launch (fused tail).
+int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from) {
+  RealView v = view_of(c);
+  cudaEvent_t stop;
+  CUDA_OR_FAIL(c, prof_begin(c, 0, &stop));
+  CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, true, (uint32_t)c->xstep,
+                                     measure_from, (double)c->J, (double)c->h, c->stream));
+  CUDA_OR_FAIL(c, prof_end(c, stop));
+  c->launches += 1;
+  c->sweep += n;
+  c->xstep += 1;
+  return RFIM_OK;
+}
+
 int do_exchange(rfim_ctx *c, int64_t measure_from) {
+  if (c->layout == RFIM_LAYOUT_BITPACK) return do_sweeps_exchange_bits(c, 0, measure_from);
   RealView v = view_of(c);
   cudaEvent_t stop;
   CUDA_OR_FAIL(c, prof_begin(c, 1, &stop));
@@ -257,10 +273,18 @@ int do_run(rfim_ctx *c, int64_t n_sweeps, int32_t ex, int64_t measure_from) {
       const int64_t to_next = ex - (c->sweep % ex);
       chunk = std::min(left, to_next);
     }
-    int rc = do_sweeps(c, chunk);
+    const bool ends_interval = ex > 0 && (c->sweep + chunk) % ex == 0;
+    int rc;
+    if (ends_interval && c->layout == RFIM_LAYOUT_BITPACK) {
+      rc = do_sweeps_exchange_bits(c, chunk, measure_from);
+      if (rc) return rc;
+      left -= chunk;
+      continue;
+    }
+    rc = do_sweeps(c, chunk);
     if (rc) return rc;
     left -= chunk;
-    if (ex > 0 && c->sweep % ex == 0) {
+    if (ends_interval) {
       rc = do_exchange(c, measure_from);
       if (rc) return rc;
     }

@@ -17,6 +17,10 @@ struct BitsPlan {
   size_t smem = 0;
   int32_t Rcap = 0;
   float4 *field4 = nullptr;  // float path: hh as float4 per (colour, word, chunk), see kernels_bits.cu
+  // fused exchange tail: per-(replica, slab) partials and the arrival counter
+  long long *partB = nullptr, *partM = nullptr, *partFi = nullptr;
+  double *partF = nullptr;
+  unsigned int *counter = nullptr;
 };
 
 bool bits_supported(int32_t L);
@@ -24,7 +28,10 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
 bool bits_plan_fits(const BitsPlan &plan, int32_t R);
 cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st);
 void free_bits_plan(BitsPlan &plan);
+// n_sweeps sweeps; when exchange is true the launch ends with exchange step j (energies, swap
+// decisions, permutation, measurement when j >= measure_from).
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
+                               bool exchange, uint32_t j, int64_t measure_from, double J, double h,
                                cudaStream_t st);
 
 }  // namespace rfim
