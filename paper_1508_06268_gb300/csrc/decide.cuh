@@ -18,16 +18,22 @@ __device__ __forceinline__ float ex2_approx(float a) {
   return r;
 }
 
-// Continuous field (Gaussian or explicit).  f = J n + hh_i in float (J n tabulated exactly as
-// the float product), x = beta dE = (s 2 beta) f, which equals fl(beta * fl(2 s f)) because the
-// factors 2 and s are exact.  Accept iff x <= 0 or u < exp(-x) with u = (word >> 8) 2^-24; the
-// comparison is done as (word >> 8) < exp(-x) 2^24 in float (the left side is exact).
-__device__ __forceinline__ bool accept_float(uint32_t word, float jn, float hh, float b2s) {
+// Continuous field (Gaussian or explicit).  f = J n + hh_i in float (J n tabulated exactly as the
+// float product): the same two roundings as the plain definition.  The table carries
+// b2l = fl(-2 beta log2 e) signed by the spin, so t = fl(b2l f) has exactly the sign of -dE and
+// 2^t = exp(-beta dE) up to the roundings of b2l and of the product.  The plain rule is: accept
+// iff dE <= 0 or u < exp(-beta dE) with u = (word >> 8) 2^-24.  Here it is evaluated as
+// rz(word) < 2^t 2^32, where rz(word) is the word rounded toward zero to a float (exactly
+// 256 (word >> 8) for words >= 2^31, at most 128 above it otherwise).  For dE <= 0, t >= 0 and
+// ex2.approx(t) >= 1 (checked over every float in [0, 1) on GB300), so the right side is >= 2^32
+// while rz(word) < 2^32: always accepted, as the rule says.  For dE > 0 the threshold differs
+// from the double-precision one by a few 2^-23 relative (ex2.approx and two float roundings),
+// and a decision can differ only when u lands that close to the threshold.
+__device__ __forceinline__ bool accept_float_l2e(uint32_t word, float jn, float hh, float b2l) {
   const float f = __fadd_rn(jn, hh);
-  const float x = __fmul_rn(b2s, f);
-  const float p24 = __fmul_rn(ex2_approx(__fmul_rn(x, -1.44269504088896340736f)), 16777216.0f);
-  const float k = __uint2float_rn(word >> 8);
-  return !(x > 0.0f) || (k < p24);
+  const float t = __fmul_rn(b2l, f);
+  const float p32 = __fmul_rn(ex2_approx(t), 4294967296.0f);
+  return __uint2float_rz(word) < p32;
 }
 
 }  // namespace rfim

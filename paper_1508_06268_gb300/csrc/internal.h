@@ -18,6 +18,7 @@ enum FieldKind : int32_t { kBimodal = 0, kGaussian = 1, kExplicit = 2 };
 //             indexed by (#up neighbours | spin << 3 | field bit << 4); accept iff word <= thr
 //   gjn     : float[8] J * (2u - 6) for u up neighbours (u = 7 unused)
 //   b2      : float[Rcap] 2 * (float)beta_k
+//   b2l     : float[Rcap] -2 * (float)beta_k * log2(e) rounded to float (bit-layout tables)
 //   beta_d  : double[Rcap] beta_k = 1 / T_k
 struct RealView {
   int32_t L, Lh, N, R;
@@ -31,6 +32,7 @@ struct RealView {
   const uint32_t *thr;
   const float *gjn;
   const float *b2;
+  const float *b2l;
   const double *beta_d;
   int32_t *t2r, *r2t;
   double *E;

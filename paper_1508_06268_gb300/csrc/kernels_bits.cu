@@ -14,29 +14,33 @@ namespace {
 
 using KernelFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *, ExchArgs);
 
-template <int L, int S, int GT>
+template <int L, int S, int GT, int NT>
 KernelFn pick(bool bim) {
-  return bim ? (KernelFn)k_sweeps_bits<L, S, GT, true> : (KernelFn)k_sweeps_bits<L, S, GT, false>;
+  return bim ? (KernelFn)k_sweeps_bits<L, S, GT, true, NT> : (KernelFn)k_sweeps_bits<L, S, GT, false, NT>;
 }
 
-KernelFn kernel_for(int L, int S, int GT, bool bim) {
-  if (L == 64) {
-    if (S == 1 && GT == 1) return pick<64, 1, 1>(bim);
-    if (S == 1 && GT == 2) return pick<64, 1, 2>(bim);
-    if (S == 2 && GT == 1) return pick<64, 2, 1>(bim);
-    if (S == 2 && GT == 2) return pick<64, 2, 2>(bim);
-    if (S == 4 && GT == 1) return pick<64, 4, 1>(bim);
-    if (S == 4 && GT == 2) return pick<64, 4, 2>(bim);
-    if (S == 4 && GT == 4) return pick<64, 4, 4>(bim);
-  } else if (L == 32) {
-    if (S == 1 && GT == 1) return pick<32, 1, 1>(bim);
-    if (S == 1 && GT == 2) return pick<32, 1, 2>(bim);
-    if (S == 2 && GT == 1) return pick<32, 2, 1>(bim);
-  } else if (L == 16) {
-    if (S == 1 && GT == 1) return pick<16, 1, 1>(bim);
-  } else if (L == 8) {
-    if (S == 1 && GT == 1) return pick<8, 1, 1>(bim);
-  }
+// Instances available to launch plans (L, cluster size S, replicas per thread GT, threads NT).
+KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
+#define RFIM_BITS_INSTANCE(l, s_, gt, nt) \
+  if (L == l && S == s_ && GT == gt && NT == nt) return pick<l, s_, gt, nt>(bim);
+  RFIM_BITS_INSTANCE(64, 1, 1, 512)
+  RFIM_BITS_INSTANCE(64, 1, 1, 1024)
+  RFIM_BITS_INSTANCE(64, 1, 2, 512)
+  RFIM_BITS_INSTANCE(64, 2, 1, 1024)
+  RFIM_BITS_INSTANCE(64, 2, 2, 512)
+  RFIM_BITS_INSTANCE(64, 2, 2, 1024)
+  RFIM_BITS_INSTANCE(64, 4, 1, 1024)
+  RFIM_BITS_INSTANCE(64, 4, 2, 512)
+  RFIM_BITS_INSTANCE(64, 4, 2, 1024)
+  RFIM_BITS_INSTANCE(64, 4, 4, 512)
+  RFIM_BITS_INSTANCE(64, 4, 4, 1024)
+  RFIM_BITS_INSTANCE(32, 1, 1, 512)
+  RFIM_BITS_INSTANCE(32, 1, 2, 512)
+  RFIM_BITS_INSTANCE(32, 2, 1, 512)
+  RFIM_BITS_INSTANCE(16, 1, 1, 512)
+  RFIM_BITS_INSTANCE(8, 1, 1, 128)
+  RFIM_BITS_INSTANCE(8, 1, 1, 512)
+#undef RFIM_BITS_INSTANCE
   return nullptr;
 }
 
@@ -80,7 +84,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (p.G > Rcap) p.G = Rcap;
   if (p.GT > p.G) p.GT = 1;
   if (p.G % p.GT) p.G = (p.G / p.GT) * p.GT;
-  KernelFn fn = kernel_for(L, p.S, p.GT, bimodal);
+  KernelFn fn = kernel_for(L, p.S, p.GT, p.threads, bimodal);
   if (!fn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
@@ -160,7 +164,9 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.partFi = plan.partFi;
   xa.partF = plan.partF;
   xa.counter = plan.counter;
-  KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, v.kind == kBimodal);
+  xa.expected = 0;  // set by the kernel to its grid size
+  xa.ctl = nullptr;
+  KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
   if (!fn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;
   cudaLaunchConfig_t cfg = {};

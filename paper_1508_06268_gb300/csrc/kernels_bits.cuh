@@ -25,7 +25,19 @@
 
 namespace rfim {
 
-// Arguments of the fused exchange tail.  Partials are [Rcap][S]; counter is zero between launches.
+// Per-realization progress kept on the device by batched launches: the last work item of a
+// realization advances it after the exchange step (sweep and exchange counters, intervals left).
+struct SlotCtl {
+  uint32_t sweep0;         // sweep index of the next interval
+  uint32_t j;              // exchange step of the next interval
+  int32_t intervals_left;  // 0: finished (its items are skipped)
+  int32_t nsw;             // sweeps per interval
+  int64_t measure_from;
+  unsigned long long done_ns;  // device time stamp when intervals_left reached 0
+};
+
+// Arguments of the fused exchange tail.  Partials are [Rcap][S]; counter is zero between launches
+// and `expected` arrivals (CTAs or work items) complete the realization.
 struct ExchArgs {
   int32_t enabled;
   uint32_t j;
@@ -34,6 +46,8 @@ struct ExchArgs {
   long long *partB, *partM, *partFi;
   double *partF;
   unsigned int *counter;
+  unsigned int expected;
+  SlotCtl *ctl;  // batched launches only (else null)
 };
 
 __host__ __device__ __forceinline__ int64_t field4_index(int c, int64_t wq, int j, int64_t wpad) {
@@ -63,11 +77,44 @@ __device__ __forceinline__ void sync_slabs() {
   }
 }
 
-// bit b of every byte of the result = bit j of the same byte of x (b, j fold to constants
-// once the chunk loop is unrolled)
-__device__ __forceinline__ uint32_t spread(uint32_t x, int b, int j) {
-  const uint32_t s = b >= j ? (x << (b - j)) : (x >> (j - b));
-  return s & (0x01010101u << b);
+// Per-site table offsets from bit slices.  For Philox block j (bits j of the four bytes) the
+// table offset of site k is bits 3..6 (float field: up-count c0 c1 c2, spin) or 2..6 (bimodal:
+// plus field bit) of byte k.  The slices are pair-interleaved once per word so that each block
+// needs one mux and one rotate (two for bimodal) instead of a shift and mask per slice.
+struct PairSlices {
+  uint32_t pa, qa, pb, qb;  // (c0,c1) and (c2,s) for even / odd blocks, (c2,s) pre-rotated by 2
+  uint32_t f3, f4;          // bimodal field bits rotated for odd / even blocks
+};
+
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int n) { return __funnelshift_l(x, x, n); }
+__device__ __forceinline__ uint32_t rotr(uint32_t x, int n) { return __funnelshift_r(x, x, n); }
+__device__ __forceinline__ uint32_t mux(uint32_t a, uint32_t b, uint32_t m) { return (a & m) | (b & ~m); }
+
+__device__ __forceinline__ PairSlices make_pairs(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t s, uint32_t f) {
+  PairSlices r;
+  r.pa = mux(c0, c1 << 1, 0x55555555u);
+  r.qa = mux(c0 >> 1, c1, 0x55555555u);
+  r.pb = rotl(mux(c2, s << 1, 0x55555555u), 2);
+  r.qb = rotl(mux(c2 >> 1, s, 0x55555555u), 2);
+  r.f4 = rotl(f, 4);
+  r.f3 = rotl(f, 3);
+  return r;
+}
+
+// j is a compile-time constant once the block loop is unrolled.
+template <bool BIM>
+__device__ __forceinline__ uint32_t block_offsets(const PairSlices &p, int j) {
+  const int m = j >> 1;
+  const uint32_t a = (j & 1) ? p.qa : p.pa;
+  const uint32_t b = (j & 1) ? p.qb : p.pb;
+  const uint32_t ma = 0x03030303u << (2 * m);  // (c0, c1) at bits 2m, 2m+1 of every byte
+  uint32_t z = mux(a, b, ma);                   // (c2, s) at 2m+2, 2m+3 (cyclic)
+  if (BIM) {
+    const uint32_t f = (j & 1) ? p.f3 : p.f4;   // field bit at 2m+4 (cyclic)
+    z = mux(f, z, rotl(0x01010101u, (2 * m + 4) & 31));
+    return rotr(z, (2 * m - 2) & 31);           // bit 2m -> bit 2 of every byte
+  }
+  return rotr(z, (2 * m - 3) & 31);             // bit 2m -> bit 3 of every byte
 }
 
 // The six other-colour neighbour words of local word (zl, iw) from plane array O (this CTA's
@@ -97,18 +144,19 @@ __device__ __forceinline__ T warp_reduce_sum(T x) {
   return x;
 }
 
+// One exchange interval of replicas [r0, r0 + gact) of realization v, slab `rank` of S: load into
+// shared memory, nsw sweeps, write back, and (xa.enabled) the energy partials and the exchange
+// tail.  All threads of the CTA call it; blockDim.x threads, dynamic shared memory >= the plan's.
 template <int L, int S, int GT, bool BIM>
-__global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint32_t sweep0, int32_t nsw,
-                                                     const float4 *__restrict__ field4, ExchArgs xa) {
+__device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, int gact, int rank, uint32_t sweep0,
+                                              int nsw, const float4 *__restrict__ field4, const ExchArgs &xa) {
   using Gm = BitsGeom<L>;
   constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
   extern __shared__ __align__(16) uint32_t sm[];
-  const int rank = S > 1 ? (int)cluster_rank() : 0;
   const int up_rank = (rank + 1) % S, dn_rank = (rank + S - 1) % S;
-  const int r0 = (int)(blockIdx.x / S) * G;
-  const int gact = min(G, v.R - r0);
   const int z0 = rank * PZ;
+  __syncthreads();  // a CTA may run several intervals back to back: shared memory is reused
   uint32_t *sp = sm;                        // [G][2][WC]
   uint32_t *tab = sm + (size_t)G * 2 * WC;  // BIM: [G][32] uint32; else [G][16] float2
   const int nt = blockDim.x, tid = threadIdx.x;
@@ -126,7 +174,7 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
     float2 *gt = reinterpret_cast<float2 *>(tab);
     for (int t = tid; t < gact * 16; t += nt) {
       const int g = t >> 4, i = t & 15;
-      const float b = v.b2[v.r2t[r0 + g]];
+      const float b = v.b2l[v.r2t[r0 + g]];
       gt[t] = make_float2(v.gjn[i & 7], (i >> 3) ? b : -b);
     }
   }
@@ -161,35 +209,31 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
           sf[gg] = sp[((size_t)g * 2 + c) * WC + wl];
           flip[gg] = 0u;
         }
-        uint32_t fb = 0;
-        if (BIM) fb = v.hbits[(int64_t)c * W + wq];
+        const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+        PairSlices ps[GT];
+#pragma unroll
+        for (int gg = 0; gg < GT; ++gg) ps[gg] = make_pairs(c0[gg], c1[gg], c2[gg], sf[gg], fb);
+        // replicas past the end of a partial group repeat the last one; only their write is skipped
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
 #pragma unroll
           for (int gg = 0; gg < GT; ++gg) {
-            const int g = grp * GT + gg;
-            if (GT > 1 && g >= gact) continue;
+            const int g = min(grp * GT + gg, gact - 1);
             const Words4 w = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), sweep, tag);
-            uint32_t acc;
-            if (BIM) {
-              acc = spread(c0[gg], 2, j) | spread(c1[gg], 3, j) | spread(c2[gg], 4, j) | spread(sf[gg], 5, j) |
-                    spread(fb, 6, j);
-            } else {
-              acc = spread(c0[gg], 3, j) | spread(c1[gg], 4, j) | spread(c2[gg], 5, j) | spread(sf[gg], 6, j);
-            }
+            const uint32_t acc = block_offsets<BIM>(ps[gg], j);
             const char *tb = reinterpret_cast<const char *>(tab) + g * 128;
             const float hk[4] = {hh4[j].x, hh4[j].y, hh4[j].z, hh4[j].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              const uint32_t off = (acc >> (8 * k)) & 0xFFu;
+              const uint32_t off = (acc >> (8 * k)) & (BIM ? 0x7Cu : 0x78u);
               bool a;
               if (BIM) {
                 a = accept_table(w.w[k], *reinterpret_cast<const uint32_t *>(tb + off));
               } else {
                 const float2 e = *reinterpret_cast<const float2 *>(tb + off);
-                a = accept_float(w.w[k], e.x, hk[k], e.y);
+                a = accept_float_l2e(w.w[k], e.x, hk[k], e.y);
               }
-              flip[gg] |= (uint32_t)a << (8 * k + j);
+              if (a) flip[gg] |= 1u << (8 * k + j);
             }
           }
         }
@@ -281,7 +325,7 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
   if (tid == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(xa.counter, 1u);
-    last_cta = prev == gridDim.x - 1;
+    last_cta = prev == xa.expected - 1;
   }
   __syncthreads();
   if (!last_cta) return;
@@ -302,7 +346,32 @@ __global__ void __launch_bounds__(512) k_sweeps_bits(RealView v, int32_t G, uint
   }
   __syncthreads();
   exchange_and_measure(v, xa.j, xa.measure_from);
-  if (tid == 0) *xa.counter = 0u;
+  if (tid == 0) {
+    *xa.counter = 0u;
+    if (xa.ctl) {
+      SlotCtl *c = xa.ctl;
+      c->sweep0 += (uint32_t)nsw;
+      c->j += 1u;
+      c->intervals_left -= 1;
+      if (c->intervals_left == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        c->done_ns = t;
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int S, int GT, bool BIM, int NT>
+__global__ void __launch_bounds__(NT) k_sweeps_bits(RealView v, int32_t G, uint32_t sweep0, int32_t nsw,
+                                                     const float4 *__restrict__ field4, ExchArgs xa) {
+  const int rank = S > 1 ? (int)cluster_rank() : 0;
+  const int r0 = (int)(blockIdx.x / S) * G;
+  const int gact = min(G, v.R - r0);
+  xa.expected = gridDim.x;
+  bits_interval<L, S, GT, BIM>(v, G, r0, gact, rank, sweep0, nsw, field4, xa);
 }
 
 }  // namespace rfim

@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8(RealView v, int colour, 
         const uint32_t idx = up | (sbit << 3) | ((uint32_t)v.hbit_c[colour * half + q] << 4);
         acc = accept_table(w.w[j], v.thr[(int64_t)k * 32 + idx]);
       } else {
-        const float b2s = sbit ? v.b2[k] : -v.b2[k];
-        acc = accept_float(w.w[j], v.gjn[up], v.hh_c[colour * half + q], b2s);
+        const float b2s = sbit ? v.b2l[k] : -v.b2l[k];
+        acc = accept_float_l2e(w.w[j], v.gjn[up], v.hh_c[colour * half + q], b2s);
       }
       if (acc) nxt ^= 1u << (8 * j);
     }

@@ -34,7 +34,7 @@ struct rfim_ctx {
   uint8_t *hbit_c = nullptr;
   uint32_t *hbits = nullptr;
   uint32_t *thr = nullptr;
-  float *gjn = nullptr, *b2 = nullptr;
+  float *gjn = nullptr, *b2 = nullptr, *b2l = nullptr;
   double *beta_d = nullptr;
   int32_t *t2r = nullptr, *r2t = nullptr;
   double *E = nullptr;
@@ -93,6 +93,7 @@ RealView view_of(const rfim_ctx *c) {
   v.thr = c->thr;
   v.gjn = c->gjn;
   v.b2 = c->b2;
+  v.b2l = c->b2l;
   v.beta_d = c->beta_d;
   v.t2r = c->t2r;
   v.r2t = c->r2t;
@@ -139,7 +140,7 @@ void free_events(rfim_ctx *c) {
 
 void free_all(rfim_ctx *c) {
   free_events(c);
-  void *ptrs[] = {c->spins8, c->bits, c->hraw, c->hh_c, c->hbit_c, c->hbits, c->thr, c->gjn, c->b2,
+  void *ptrs[] = {c->spins8, c->bits, c->hraw, c->hh_c, c->hbit_c, c->hbits, c->thr, c->gjn, c->b2, c->b2l,
                   c->beta_d, c->t2r, c->r2t, c->E, c->M, c->att, c->acc, c->obs, c->n_meas, c->scratch8};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -175,17 +176,19 @@ void bimodal_row(double beta, float J, float h, uint32_t out[32]) {
 int upload_temps(rfim_ctx *c) {
   const int32_t R = c->R;
   std::vector<uint32_t> thr((size_t)R * 32);
-  std::vector<float> b2(R);
+  std::vector<float> b2(R), b2l(R);
   std::vector<double> beta(R);
   for (int32_t k = 0; k < R; ++k) {
     beta[k] = 1.0 / c->T[k];
     b2[k] = 2.0f * (float)beta[k];
+    b2l[k] = (float)(-1.4426950408889634 * (double)b2[k]);
     bimodal_row(beta[k], c->J, c->h, &thr[(size_t)k * 32]);
   }
   float gjn[8];
   for (int u = 0; u < 8; ++u) gjn[u] = c->J * (float)(2 * u - 6);
   CUDA_OR_FAIL(c, cudaMemcpyAsync(c->thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_OR_FAIL(c, cudaMemcpyAsync(c->b2, b2.data(), R * 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(c->b2l, b2l.data(), R * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_OR_FAIL(c, cudaMemcpyAsync(c->beta_d, beta.data(), R * 8, cudaMemcpyHostToDevice, c->stream));
   CUDA_OR_FAIL(c, cudaMemcpyAsync(c->gjn, gjn, sizeof gjn, cudaMemcpyHostToDevice, c->stream));
   // pageable sources: make sure the copies have consumed the host vectors before they go away
@@ -370,6 +373,7 @@ int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
   if ((rc = dalloc(c, &c->thr, (size_t)Rcap * 32))) return bail(rc);
   if ((rc = dalloc(c, &c->gjn, 8))) return bail(rc);
   if ((rc = dalloc(c, &c->b2, Rcap))) return bail(rc);
+  if ((rc = dalloc(c, &c->b2l, Rcap))) return bail(rc);
   if ((rc = dalloc(c, &c->beta_d, Rcap))) return bail(rc);
   if ((rc = dalloc(c, &c->t2r, Rcap))) return bail(rc);
   if ((rc = dalloc(c, &c->r2t, Rcap))) return bail(rc);
