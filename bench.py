@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--sweeps", type=int, default=SWEEPS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--workload", default="c4", choices=["c4", "serve"])
+    p.add_argument("--realizations", type=int, default=128)
+    p.add_argument("--serve-sweeps", type=int, default=2000)
+    p.add_argument("--int-rates", action="store_true")
     return p.parse_args()
 
 
@@ -154,10 +158,108 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_R = {8: 16, 16: 32, 32: 64, 64: 128}
+
+
+def serve_requests(n, sweeps):
+    """C5-shaped request stream: L uniform in {8,16,32,64} (seed 7), R matched to L, Gaussian h=1,
+    Poisson arrival gaps of unit mean (seed 2024; scaled by the caller)."""
+    rng = np.random.default_rng(7)
+    Ls = rng.choice([8, 16, 32, 64], size=n)
+    gaps = np.random.default_rng(2024).exponential(1.0, size=n)
+    return [(int(L), SERVE_R[int(L)], i) for i, L in enumerate(Ls)], gaps
+
+
+def run_serve(args):
+    """Continuous batching vs plain per-realization launches on the same request stream."""
+    import torch
+    import paper_1508_06268_gb300 as rf
+    from paper_1508_06268_gb300 import inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs, gaps = serve_requests(args.realizations, args.serve_sweeps)
+    ex, sw = EX, args.serve_sweeps
+    mf = sw // ex // 2
+    temps = {L: inputs.geometric_temps(T_MIN, T_MAX, R_) for L, R_ in SERVE_R.items()}
+    work = sum(L ** 3 * R_ * sw for L, R_, _ in reqs)
+
+    def batched(arrivals):
+        srv = rf.Server(mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4)
+        t0 = time.perf_counter()
+        pend, lat, i = {}, [], 0
+        while len(lat) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
+                L, R_, k = reqs[i]
+                pend[srv.submit(L, temps[L], sw, ex, mf, field_kind=rf.FIELD_GAUSSIAN, field_seed=1 + k,
+                                realization=k)] = arrivals[i]
+                i += 1
+            for t in list(pend):
+                r = srv.poll(t)
+                if r is not None:
+                    lat.append(r["latency_s"])
+                    del pend[t]
+            time.sleep(0.0002)
+        span = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return np.array(lat), span, st
+
+    def sequential(arrivals):
+        t0 = time.perf_counter()
+        lat = []
+        for (L, R_, k), a in zip(reqs, arrivals):
+            while time.perf_counter() - t0 < a:
+                time.sleep(0.0002)
+            g = rf.Realization(L, temps[L], field_kind=rf.FIELD_GAUSSIAN, field_seed=1 + k, realization=k,
+                               layout=rf.LAYOUT_BITPACK)
+            g.run(sw, ex, mf)
+            g.observables()
+            g.close()
+            lat.append(time.perf_counter() - t0 - a)
+        return np.array(lat), time.perf_counter() - t0
+
+    # warm-up (module load, graph capture), then the closed-loop capacity of the batched server
+    batched(np.zeros(len(reqs)))
+    _, span_closed, _ = batched(np.zeros(len(reqs)))
+    rate = 0.8 * len(reqs) / span_closed  # realizations / s offered to both servers
+    arrivals = np.cumsum(gaps) / rate
+    arrivals -= arrivals[0]
+    lat_b, span_b, st = batched(arrivals)
+    lat_s, span_s = sequential(arrivals)
+    line = {
+        "metric": "served realizations: p50/p99 latency and spin-flip attempts/ns (batched vs per-realization)",
+        "workload": "C5-shaped: Gaussian h=1, L uniform in {8,16,32,64}, R=16/32/64/128",
+        "realizations": len(reqs), "sweeps_each": sw, "exchange_every": ex,
+        "offered_rate_per_s": rate, "arrivals": "Poisson (seed 2024), 0.8 x closed-loop batched capacity",
+        "batched": {"p50_s": float(np.percentile(lat_b, 50)), "p99_s": float(np.percentile(lat_b, 99)),
+                    "attempts_per_ns": work / (span_b * 1e9), "makespan_s": span_b,
+                    "closed_loop_attempts_per_ns": work / (span_closed * 1e9),
+                    "graph_launches": st["graph_launches"], "grid": st["grid"]},
+        "per_realization": {"p50_s": float(np.percentile(lat_s, 50)), "p99_s": float(np.percentile(lat_s, 99)),
+                            "attempts_per_ns": work / (span_s * 1e9), "makespan_s": span_s},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_int_rates():
+    """Builds and runs the GB300 issue-rate microbenchmark (the roofline's peak basis)."""
+    src = os.path.join(ROOT, "paper_1508_06268_gb300", "microbench", "int_rates.cu")
+    exe = os.path.join(ROOT, "paper_1508_06268_gb300", "_lib", "int_rates")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    subprocess.run([exe], check=True)
+
+
 def main():
     args = parse()
+    if args.int_rates:
+        run_int_rates()
+        return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     import torch
     import paper_1508_06268_gb300 as rf

@@ -153,6 +153,42 @@ const char *rfim_last_error(const rfim_ctx *ctx);
 /* Number of kernel launches this context has enqueued since creation. */
 int64_t rfim_launch_count(const rfim_ctx *ctx);
 
+/* ---- Serving: continuous batching of independent disorder realizations -------------------------
+   The quenched average (Sec. 7) needs many independent realizations.  A server owns a device
+   memory arena and a worker thread: submitted realizations are admitted in arrival order as slots
+   and arena memory free up; all resident ones advance together, intervals_per_launch exchange
+   intervals per replay of a captured CUDA graph of persistent batched kernels; finished ones are
+   retired between replays and their observables kept until polled.  Each result is the same as
+   the realization run alone through the server (nothing is shared between realizations).  The
+   bit layout is used (L in {8, 16, 32, 64}, R <= 1024). */
+typedef struct rfim_server rfim_server;
+typedef struct {
+  uint64_t mem_budget_bytes;    /* device arena for resident realizations (admission control) */
+  int32_t max_slots;            /* realizations resident at the same time, >= 1 */
+  int32_t intervals_per_launch; /* exchange intervals per graph replay, >= 1 */
+} rfim_server_config;
+typedef struct {
+  int64_t queued, resident, completed, graph_launches;
+  double busy_s;   /* seconds spent in graph replays */
+  double attempts; /* spin-flip attempts of completed realizations */
+  int32_t grid;    /* CTAs of the persistent batched kernel */
+} rfim_server_info;
+/* Errors: RFIM_EINVAL (bad configuration), RFIM_ENOMEM (arena), RFIM_ECUDA. */
+int rfim_server_create(const rfim_server_config *cfg, rfim_server **out);
+/* Queues one realization (cfg as for rfim_create; cfg->layout and cfg->stream are ignored, host
+   arrays are copied before return) for n_sweeps sweeps, a positive multiple of exchange_every,
+   with measurements from exchange step measure_from on.  *ticket identifies it. */
+int rfim_server_submit(rfim_server *s, const rfim_config *cfg, int64_t n_sweeps, int32_t exchange_every,
+                       int64_t measure_from, uint64_t *ticket);
+/* RFIM_EBUSY while queued or running; RFIM_OK once finished: fills out (caller-owned arrays sized
+   for its R, any may be NULL) and *latency_s (seconds from submit to retirement), then forgets the
+   ticket.  RFIM_EINVAL for an unknown ticket; RFIM_ENOMEM if the realization cannot fit. */
+int rfim_server_poll(rfim_server *s, uint64_t ticket, rfim_obs *out, double *latency_s);
+int rfim_server_stats(rfim_server *s, rfim_server_info *out);
+/* Stops the worker (resident work is abandoned) and frees everything.  NULL is accepted. */
+int rfim_server_destroy(rfim_server *s);
+const char *rfim_server_last_error(const rfim_server *s);
+
 /* Kernel timing.  rfim_profile(ctx, 1) clears earlier records and starts bracketing every
    sweep-kernel launch group (one rfim_sweep / exchange-interval worth of sweeps) and every
    energy + exchange pair with CUDA events on the context's stream; rfim_profile(ctx, 0) stops.

@@ -42,6 +42,17 @@ class Obs(C.Structure):
                 ("acc", C.c_void_p), ("n_meas", C.c_int64)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
+                ("intervals_per_launch", C.c_int32)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("resident", C.c_int64), ("completed", C.c_int64),
+                ("graph_launches", C.c_int64), ("busy_s", C.c_double), ("attempts", C.c_double),
+                ("grid", C.c_int32)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -71,12 +82,20 @@ def load():
             L.rfim_launch_count.argtypes = [P]
             L.rfim_launch_count.restype = i64
             L.rfim_selftest_bits.argtypes = [i32, u32]
+            L.rfim_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
+            L.rfim_server_submit.argtypes = [P, C.POINTER(Config), i64, i32, i64, C.POINTER(C.c_uint64)]
+            L.rfim_server_poll.argtypes = [P, C.c_uint64, C.POINTER(Obs), C.POINTER(C.c_double)]
+            L.rfim_server_stats.argtypes = [P, C.POINTER(ServerInfo)]
+            L.rfim_server_destroy.argtypes = [P]
+            L.rfim_server_last_error.argtypes = [P]
+            L.rfim_server_last_error.restype = C.c_char_p
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
             for name in ("rfim_create", "rfim_destroy", "rfim_sweep", "rfim_exchange", "rfim_run",
                          "rfim_adapt_temps", "rfim_observables", "rfim_get_state", "rfim_set_state",
                          "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
-                         "rfim_profile_read"):
+                         "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
+                         "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -215,3 +234,99 @@ class Realization:
     @property
     def launch_count(self):
         return int(self._lib.rfim_launch_count(self._h))
+
+
+class Server:
+    """Continuous-batching server of independent realizations (include/rfim.h, serving section)."""
+
+    def __init__(self, mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4):
+        self._lib = load()
+        self._h = None
+        cfg = ServerConfig(mem_budget_bytes, max_slots, intervals_per_launch)
+        out = C.c_void_p()
+        rc = self._lib.rfim_server_create(C.byref(cfg), C.byref(out))
+        if rc != OK:
+            raise RfimError(rc, self._lib.rfim_server_last_error(None).decode())
+        self._h = out
+        self._R = {}
+
+    def close(self):
+        if self._h:
+            self._lib.rfim_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _err(self, rc):
+        return RfimError(rc, self._lib.rfim_server_last_error(self._h).decode())
+
+    def submit(self, L, temps, n_sweeps, exchange_every, measure_from=0, *, J=1.0, h=1.0,
+               field_kind=FIELD_GAUSSIAN, field=None, field_seed=1, seed=42, realization=0):
+        temps = np.ascontiguousarray(temps, dtype=np.float64)
+        fld = None if field is None else np.ascontiguousarray(field, dtype=np.float32)
+        cfg = Config()
+        cfg.L, cfg.R, cfg.R_capacity = L, len(temps), len(temps)
+        cfg.J, cfg.h, cfg.field_kind = J, h, field_kind
+        cfg.field = None if fld is None else fld.ctypes.data
+        cfg.field_seed, cfg.seed, cfg.realization = field_seed, seed, realization
+        cfg.temps = temps.ctypes.data
+        cfg.layout, cfg.stream = LAYOUT_BITPACK, None
+        t = C.c_uint64()
+        rc = self._lib.rfim_server_submit(self._h, C.byref(cfg), n_sweeps, exchange_every,
+                                          measure_from, C.byref(t))
+        if rc != OK:
+            raise self._err(rc)
+        self._R[t.value] = len(temps)
+        return t.value
+
+    def poll(self, ticket):
+        """None while queued or running; the observables dict (plus latency_s) once finished."""
+        R = self._R.get(ticket, 2)
+        arrs = {k: np.zeros(R, dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4")}
+        att = np.zeros(max(R - 1, 1), dtype=np.uint64)
+        acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
+        o = Obs()
+        for k, a in arrs.items():
+            setattr(o, k, a.ctypes.data)
+        o.att, o.acc = att.ctypes.data, acc.ctypes.data
+        lat = C.c_double()
+        rc = self._lib.rfim_server_poll(self._h, ticket, C.byref(o), C.byref(lat))
+        if rc == EBUSY:
+            return None
+        if rc != OK:
+            self._R.pop(ticket, None)
+            raise self._err(rc)
+        self._R.pop(ticket, None)
+        arrs["att"], arrs["acc"] = att[:R - 1], acc[:R - 1]
+        arrs["n_meas"] = int(o.n_meas)
+        arrs["sums"] = np.stack([arrs[k] for k in ("e", "e2", "absm", "m2", "m4")], axis=1)
+        arrs["latency_s"] = lat.value
+        return arrs
+
+    def wait(self, ticket, timeout_s=600.0, interval_s=0.0005):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"ticket {ticket} not finished after {timeout_s} s")
+            time.sleep(interval_s)
+
+    def stats(self):
+        info = ServerInfo()
+        rc = self._lib.rfim_server_stats(self._h, C.byref(info))
+        if rc != OK:
+            raise self._err(rc)
+        return {k: getattr(info, k) for k, _ in ServerInfo._fields_}

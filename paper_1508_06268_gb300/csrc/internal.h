@@ -42,6 +42,12 @@ struct RealView {
   int64_t *n_meas;
 };
 
+// host_tables.cu: bimodal thresholds (thr - 1, 32 entries per temperature), b2 = 2 beta,
+// b2l = -2 beta log2 e, beta = 1/T, gjn[u] = J (2u - 6)
+void bimodal_row(double beta, float J, float h, uint32_t out[32]);
+void temperature_tables(const double *T, int32_t R, float J, float h, uint32_t *thr, float *b2, float *b2l,
+                        double *beta, float gjn[8]);
+
 // kernels_common.cu
 cudaError_t launch_field(const RealView &v, int32_t kind, uint32_t field_seed, float h, float *hraw,
                          float *hh_c, uint8_t *hbit_c, uint32_t *hbits, cudaStream_t st);

@@ -213,9 +213,17 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
         PairSlices ps[GT];
 #pragma unroll
         for (int gg = 0; gg < GT; ++gg) ps[gg] = make_pairs(c0[gg], c1[gg], c2[gg], sf[gg], fb);
-        // replicas past the end of a partial group repeat the last one; only their write is skipped
+        // replicas past the end of a partial group repeat the last one; only their write is skipped.
+        // Float field: the acceptance of site (j, k) is the sign bit of rz(word) - 2^t 2^32, shifted
+        // into fk[k] (blocks visited j = 7..0, so block j ends at bit j); flip = fk[k] << 8k.
+        uint32_t fk[GT][4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int gg = 0; gg < GT; ++gg)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) fk[gg][k] = 0u;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = 7 - jj;
 #pragma unroll
           for (int gg = 0; gg < GT; ++gg) {
             const int g = min(grp * GT + gg, gact - 1);
@@ -226,16 +234,18 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const uint32_t off = (acc >> (8 * k)) & (BIM ? 0x7Cu : 0x78u);
-              bool a;
               if (BIM) {
-                a = accept_table(w.w[k], *reinterpret_cast<const uint32_t *>(tb + off));
+                if (accept_table(w.w[k], *reinterpret_cast<const uint32_t *>(tb + off))) flip[gg] |= 1u << (8 * k + j);
               } else {
                 const float2 e = *reinterpret_cast<const float2 *>(tb + off);
-                a = accept_float_l2e(w.w[k], e.x, hk[k], e.y);
+                fk[gg][k] = __funnelshift_l(accept_float_sign(w.w[k], e.x, hk[k], e.y), fk[gg][k], 1);
               }
-              if (a) flip[gg] |= 1u << (8 * k + j);
             }
           }
+        }
+        if (!BIM) {
+#pragma unroll
+          for (int gg = 0; gg < GT; ++gg) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
         }
 #pragma unroll
         for (int gg = 0; gg < GT; ++gg) {

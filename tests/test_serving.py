@@ -1,0 +1,89 @@
+"""Serving / continuous batching (GPU): each realization's result in a mixed batch equals the same
+realization served alone and, for the bimodal field, the oracle bit for bit; admission control by
+device-memory budget; errors reported at the boundary."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_06268_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1508_06268_gb300 as rf  # noqa: E402
+
+MIX = [  # (L, R, field kind, realization)
+    (8, 16, rf.FIELD_GAUSSIAN, 0), (16, 8, rf.FIELD_BIMODAL, 1), (32, 6, rf.FIELD_GAUSSIAN, 2),
+    (64, 4, rf.FIELD_GAUSSIAN, 3), (8, 5, rf.FIELD_BIMODAL, 4), (16, 12, rf.FIELD_GAUSSIAN, 5),
+    (32, 9, rf.FIELD_BIMODAL, 6), (64, 3, rf.FIELD_BIMODAL, 7),
+]
+SWEEPS, EX = 40, 10
+
+
+def submit(srv, L, R, kind, real, sweeps=SWEEPS):
+    return srv.submit(L, inputs.geometric_temps(1.0, 5.0, R), sweeps, EX, 1, field_kind=kind,
+                      h=1.5 if kind == rf.FIELD_BIMODAL else 1.0, field_seed=10 + real, seed=42,
+                      realization=real)
+
+
+def test_results_same_alone_and_in_the_mix():
+    with rf.Server(mem_budget_bytes=256 << 20, max_slots=16, intervals_per_launch=2) as srv:
+        tickets = [submit(srv, *m) for m in MIX]
+        mixed = [srv.wait(t) for t in tickets]
+    for m, res in zip(MIX, mixed):
+        with rf.Server(mem_budget_bytes=64 << 20, max_slots=1, intervals_per_launch=3) as solo:
+            alone = solo.wait(submit(solo, *m))
+        np.testing.assert_array_equal(res["sums"], alone["sums"], err_msg=str(m))
+        np.testing.assert_array_equal(res["acc"], alone["acc"], err_msg=str(m))
+        assert res["n_meas"] == alone["n_meas"] == SWEEPS // EX - 1
+
+
+@pytest.mark.parametrize("L,R,real", [(8, 5, 4), (16, 8, 1), (32, 9, 6), (64, 3, 7)])
+def test_bimodal_served_equals_oracle(L, R, real):
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    with rf.Server(mem_budget_bytes=64 << 20, max_slots=2) as srv:
+        res = srv.wait(submit(srv, L, R, rf.FIELD_BIMODAL, real))
+    o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=10 + real, seed=42,
+                      realization=real)
+    o.run(SWEEPS, EX, 1)
+    np.testing.assert_array_equal(res["sums"], o.observables())
+    att, acc = o.exchange_stats()
+    np.testing.assert_array_equal(res["att"], att)
+    np.testing.assert_array_equal(res["acc"], acc)
+
+
+def test_admission_by_memory_budget():
+    # budget for two L=32, R=16 Gaussian realizations (about 0.5 MB each) at a time
+    with rf.Server(mem_budget_bytes=1_100_000, max_slots=8, intervals_per_launch=1) as srv:
+        tickets = [submit(srv, 32, 16, rf.FIELD_GAUSSIAN, r, sweeps=20) for r in range(6)]
+        peak = 0
+        results = {}
+        while len(results) < len(tickets):
+            peak = max(peak, srv.stats()["resident"])
+            for t in tickets:
+                if t not in results:
+                    r = srv.poll(t)
+                    if r is not None:
+                        results[t] = r
+        st = srv.stats()
+    assert st["completed"] == 6 and st["queued"] == 0
+    assert 1 <= peak <= 2
+
+
+def test_errors_at_the_boundary():
+    with rf.Server(mem_budget_bytes=2 << 20, max_slots=2) as srv:
+        with pytest.raises(rf.RfimError):
+            srv.submit(12, inputs.geometric_temps(1.0, 5.0, 4), 20, 10)  # unsupported L
+        with pytest.raises(rf.RfimError):
+            srv.submit(8, inputs.geometric_temps(1.0, 5.0, 4), 25, 10)  # not a multiple
+        with pytest.raises(rf.RfimError):
+            srv.poll(12345)  # unknown ticket
+        t = srv.submit(64, inputs.geometric_temps(1.0, 5.0, 64), 10, 10)  # larger than the budget
+        with pytest.raises(rf.RfimError) as e:
+            srv.wait(t, timeout_s=60)
+        assert e.value.code == rf.ENOMEM
