@@ -189,6 +189,45 @@ int rfim_server_stats(rfim_server *s, rfim_server_info *out);
 int rfim_server_destroy(rfim_server *s);
 const char *rfim_server_last_error(const rfim_server *s);
 
+/* ---- Exchange step without device allocation ------------------------------------------------------
+   The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+   device memory: a framework or arena that owns all of the device memory, a latency-critical loop
+   in which cudaMalloc / cudaFree would synchronise the device, or code recorded into a CUDA graph.
+   It computes every replica's energy (Eq. 1) from caller-owned buffers and takes exchange step j
+   exactly as rfim_exchange does (Eq. 2, Sec. 3.3; measurement of Sec. 7 when j >= measure_from),
+   enqueued on `stream`.  It allocates nothing: its scratch (partial sums per replica and z slab,
+   and an arrival counter) is a file-scope device array of 512 KiB that every GPU loading the
+   library holds until exit.  R times the number of z slabs must fit 16384 slots (RFIM_EINVAL
+   otherwise, message in rfim_last_error(NULL)).  The first call on a device sets the array up
+   (looks up its device address and clears the counter, synchronising `stream`); make that first
+   call before any stream capture.  All calls share the array, which keeps the last call's
+   contents: calls that overlap on the GPU race and must not be issued.
+   Buffers (all device pointers, caller-owned):
+     spins : uint32[R][2][L^3/64] bit layout: for colour c = (x+y+z) mod 2 the site with
+             q = (x>>1) + (L/2)(y + L z) is bit 8(q&3) + ((q&31)>>2) of word q>>5 (1 = up)
+     field : float[L^3] unscaled h_i in natural order (bimodal: +-1, exact integer field term;
+             otherwise float arithmetic on hh_i = (float)h * h_i)
+     beta  : double[R] 1/T_k in ascending-temperature order
+     t2r, r2t (int32[R], in/out), att, acc (uint64[R-1], in/out), obs (double[R][5], in/out),
+     n_meas (int64, in/out), E (double[R], out), M (int64[R], out). */
+typedef struct {
+  int32_t L;           /* 8, 16, 32 or 64 */
+  int32_t R;           /* >= 2 */
+  float J, h;
+  int32_t field_kind;  /* RFIM_FIELD_* */
+  uint32_t seed, realization, stage;
+  const uint32_t *spins;
+  const float *field;
+  const double *beta;
+  int32_t *t2r, *r2t;
+  uint64_t *att, *acc;
+  double *obs;
+  int64_t *n_meas;
+  double *E;
+  int64_t *M;
+} rfim_exchange_buffers;
+int rfim_exchange_noalloc(const rfim_exchange_buffers *b, uint32_t j, int64_t measure_from, void *stream);
+
 /* Kernel timing.  rfim_profile(ctx, 1) clears earlier records and starts bracketing every
    sweep-kernel launch group (one rfim_sweep / exchange-interval worth of sweeps) and every
    energy + exchange pair with CUDA events on the context's stream; rfim_profile(ctx, 0) stops.

@@ -42,6 +42,16 @@ class Obs(C.Structure):
                 ("acc", C.c_void_p), ("n_meas", C.c_int64)]
 
 
+class ExchangeBuffers(C.Structure):
+    """rfim_exchange_buffers: caller-owned device buffers of the allocation-free exchange step."""
+    _fields_ = [("L", C.c_int32), ("R", C.c_int32), ("J", C.c_float), ("h", C.c_float),
+                ("field_kind", C.c_int32), ("seed", C.c_uint32), ("realization", C.c_uint32),
+                ("stage", C.c_uint32), ("spins", C.c_void_p), ("field", C.c_void_p),
+                ("beta", C.c_void_p), ("t2r", C.c_void_p), ("r2t", C.c_void_p), ("att", C.c_void_p),
+                ("acc", C.c_void_p), ("obs", C.c_void_p), ("n_meas", C.c_void_p), ("E", C.c_void_p),
+                ("M", C.c_void_p)]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
                 ("intervals_per_launch", C.c_int32)]
@@ -89,13 +99,15 @@ def load():
             L.rfim_server_destroy.argtypes = [P]
             L.rfim_server_last_error.argtypes = [P]
             L.rfim_server_last_error.restype = C.c_char_p
+            L.rfim_exchange_noalloc.argtypes = [C.POINTER(ExchangeBuffers), u32, i64, P]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
             for name in ("rfim_create", "rfim_destroy", "rfim_sweep", "rfim_exchange", "rfim_run",
                          "rfim_adapt_temps", "rfim_observables", "rfim_get_state", "rfim_set_state",
                          "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
                          "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
-                         "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy"):
+                         "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
+                         "rfim_exchange_noalloc"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -108,6 +120,15 @@ def _ptr(a):
 def _current_stream():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def exchange_noalloc(buffers: ExchangeBuffers, j: int, measure_from: int, stream=None) -> None:
+    """rfim_exchange_noalloc on caller-owned device buffers (no allocation by the library)."""
+    lib = load()
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    rc = lib.rfim_exchange_noalloc(C.byref(buffers), j, measure_from, st)
+    if rc != OK:
+        raise RfimError(rc, lib.rfim_last_error(None).decode())
 
 
 def selftest_bits(L: int, seed: int = 1) -> int:

@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of librfim (not part of the C ABI).
 #pragma once
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace rfim {
@@ -41,6 +43,9 @@ struct RealView {
   double *obs;
   int64_t *n_meas;
 };
+
+// rfim_api.cu: records msg as the calling thread's last error (rfim_last_error(NULL)); returns code
+int set_thread_error(int code, const std::string &msg);
 
 // host_tables.cu: bimodal thresholds (thr - 1, 32 entries per temperature), b2 = 2 beta,
 // b2l = -2 beta log2 e, beta = 1/T, gjn[u] = J (2u - 6)

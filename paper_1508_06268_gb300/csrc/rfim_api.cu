@@ -277,6 +277,11 @@ int dalloc(rfim_ctx *c, T **p, size_t count) {
 
 }  // namespace
 
+int rfim::set_thread_error(int code, const std::string &msg) {
+  g_create_error = msg;
+  return code;
+}
+
 extern "C" {
 
 int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
