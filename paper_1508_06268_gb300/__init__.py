@@ -100,6 +100,7 @@ def load():
             L.rfim_server_last_error.argtypes = [P]
             L.rfim_server_last_error.restype = C.c_char_p
             L.rfim_exchange_noalloc.argtypes = [C.POINTER(ExchangeBuffers), u32, i64, P]
+            L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
             for name in ("rfim_create", "rfim_destroy", "rfim_sweep", "rfim_exchange", "rfim_run",
@@ -107,7 +108,7 @@ def load():
                          "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
                          "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
                          "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
-                         "rfim_exchange_noalloc"):
+                         "rfim_exchange_noalloc", "rfim_tune"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -129,6 +130,17 @@ def exchange_noalloc(buffers: ExchangeBuffers, j: int, measure_from: int, stream
     rc = lib.rfim_exchange_noalloc(C.byref(buffers), j, measure_from, st)
     if rc != OK:
         raise RfimError(rc, lib.rfim_last_error(None).decode())
+
+
+def tune(L: int, R: int, field_kind: int = FIELD_GAUSSIAN):
+    """Runs the launch-shape tuner; returns ("S,G,GT,threads", attempts/ns of the best shape)."""
+    lib = load()
+    buf = C.create_string_buffer(64)
+    rate = C.c_double()
+    rc = lib.rfim_tune(L, R, field_kind, buf, 64, C.byref(rate))
+    if rc != OK:
+        raise RfimError(rc, lib.rfim_last_error(None).decode())
+    return buf.value.decode(), rate.value
 
 
 def selftest_bits(L: int, seed: int = 1) -> int:

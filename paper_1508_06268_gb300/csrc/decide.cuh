@@ -36,13 +36,14 @@ __device__ __forceinline__ bool accept_float_l2e(uint32_t word, float jn, float 
   return __uint2float_rz(word) < p32;
 }
 
-// The same test as a sign bit: bit 31 of the result is 1 iff the move is accepted
-// (rz(word) - p32 is negative exactly when rz(word) < p32; equal values give +0).
+// The same test as a sign bit: bit 31 of the result is 1 iff the move is accepted.  One FMA
+// forms rz(word) - 2^t 2^32 with a single rounding; the product is exact (a power-of-two scaling)
+// so the result is the correctly rounded difference, negative exactly when rz(word) < p32 and
+// +0 when they are equal.
 __device__ __forceinline__ uint32_t accept_float_sign(uint32_t word, float jn, float hh, float b2l) {
   const float f = __fadd_rn(jn, hh);
   const float t = __fmul_rn(b2l, f);
-  const float p32 = __fmul_rn(ex2_approx(t), 4294967296.0f);
-  return __float_as_uint(__fsub_rn(__uint2float_rz(word), p32));
+  return __float_as_uint(__fmaf_rn(ex2_approx(t), -4294967296.0f, __uint2float_rz(word)));
 }
 
 }  // namespace rfim

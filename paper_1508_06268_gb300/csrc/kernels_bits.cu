@@ -1,7 +1,10 @@
 // Launch plan, dispatch and helpers of the bit-layout sweep kernel (kernels_bits.cuh).
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels_bits.cuh"
@@ -61,6 +64,26 @@ __global__ void k_build_field4(RealView v, float4 *field4, int64_t wpad) {
 
 bool bits_supported(int32_t L) { return L == 8 || L == 16 || L == 32 || L == 64; }
 
+namespace {
+thread_local const char *t_plan_override = nullptr;
+std::mutex g_tuned_mu;
+std::map<std::tuple<int, int, bool>, std::string> g_tuned;  // (L, R, bimodal) -> "S,G,GT,threads"
+}  // namespace
+
+void set_plan_override(const char *plan) { t_plan_override = plan; }
+
+void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &plan) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  g_tuned[{L, R, bimodal}] = plan;
+}
+
+std::vector<std::string> plan_candidates(int32_t L) {
+  if (L == 64) return {"4,4,4,512", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "2,2,2,1024", "1,1,1,1024", "1,1,1,512"};
+  if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512"};
+  if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
+  return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
+}
+
 int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err) {
   BitsPlan p;
   p.L = L;
@@ -74,8 +97,16 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   } else {
     p.S = 1; p.G = 16; p.GT = 1; p.threads = 128;
   }
-  // "S,G,GT,threads" override (used by the launch-shape tuner and the benchmarks)
-  if (const char *o = getenv("RFIM_BITS_PLAN")) {
+  // "S,G,GT,threads": the tuner's current candidate, else a tuned shape for this (L, R, field),
+  // else the RFIM_BITS_PLAN environment override, else the defaults above
+  std::string tuned;
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find({L, Rcap, bimodal});
+    if (it != g_tuned.end()) tuned = it->second;
+  }
+  const char *o = t_plan_override ? t_plan_override : (!tuned.empty() ? tuned.c_str() : getenv("RFIM_BITS_PLAN"));
+  if (o) {
     int s, g, gt, th;
     if (sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;

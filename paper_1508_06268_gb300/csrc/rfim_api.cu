@@ -554,6 +554,59 @@ const char *rfim_last_error(const rfim_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 int64_t rfim_launch_count(const rfim_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+int rfim_tune(int32_t L, int32_t R, int32_t field_kind, char *plan_out, int32_t plan_cap, double *attempts_per_ns) {
+  if (!bits_supported(L) || R < 2 || field_kind < 0 || field_kind > 2)
+    return fail(nullptr, RFIM_EINVAL, "rfim_tune: L in {8,16,32,64}, R >= 2, known field kind");
+  const bool bim = field_kind == RFIM_FIELD_BIMODAL;
+  std::vector<double> T(R);
+  for (int32_t k = 0; k < R; ++k) T[k] = 1.0 * std::pow(5.0, (double)k / (R - 1));
+  std::vector<float> field;
+  if (field_kind == RFIM_FIELD_EXPLICIT) field.assign((size_t)L * L * L, 0.5f);
+  rfim_config cfg{};
+  cfg.L = L;
+  cfg.R = R;
+  cfg.R_capacity = R;
+  cfg.J = 1.0f;
+  cfg.h = 1.0f;
+  cfg.field_kind = field_kind;
+  cfg.field = field.empty() ? nullptr : field.data();
+  cfg.field_seed = 1;
+  cfg.seed = 7;
+  cfg.temps = T.data();
+  cfg.layout = RFIM_LAYOUT_BITPACK;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(nullptr, RFIM_ECUDA, "rfim_tune: stream");
+  cfg.stream = st;
+  const int64_t intervals = L >= 32 ? 20 : 50, ex = 10;
+  std::string best;
+  double best_rate = 0.0;
+  for (const std::string &cand : plan_candidates(L)) {
+    set_plan_override(cand.c_str());
+    rfim_ctx *c = nullptr;
+    const int rc = rfim_create(&cfg, &c);
+    set_plan_override(nullptr);
+    if (rc != RFIM_OK) continue;  // shape not available for this R (or does not fit)
+    double ms = 0.0;
+    int64_t launches = 0;
+    bool ok = do_run(c, 2 * ex, ex, INT64_MAX) == RFIM_OK && rfim_profile(c, 1) == RFIM_OK &&
+              do_run(c, intervals * ex, ex, INT64_MAX) == RFIM_OK &&
+              rfim_profile_read(c, &ms, &launches, nullptr, nullptr) == RFIM_OK && ms > 0.0;
+    rfim_destroy(c);
+    if (!ok) continue;
+    const double rate = (double)L * L * L * R * intervals * ex / (ms * 1e6);
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = cand;
+    }
+  }
+  cudaStreamDestroy(st);
+  if (best.empty()) return fail(nullptr, RFIM_ECUDA, "rfim_tune: no launch shape ran");
+  remember_tuned_plan(L, R, bim, best);
+  if (plan_out && plan_cap > 0) snprintf(plan_out, plan_cap, "%s", best.c_str());
+  if (attempts_per_ns) *attempts_per_ns = best_rate;
+  return RFIM_OK;
+}
+
 int rfim_profile(rfim_ctx *ctx, int enable) {
   if (!ctx) return RFIM_EINVAL;
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -24,6 +25,11 @@ struct BitsPlan {
 };
 
 bool bits_supported(int32_t L);
+// Launch-shape tuner support: a thread-local candidate shape for the next make_bits_plan, the
+// remembered best shape per (L, R, field kind), and the candidates instantiated for each L.
+void set_plan_override(const char *plan);
+void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &plan);
+std::vector<std::string> plan_candidates(int32_t L);
 int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err);
 bool bits_plan_fits(const BitsPlan &plan, int32_t R);
 cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st);
