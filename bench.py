@@ -35,6 +35,10 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 32 of them per SM per clock on GB300 (measured), which bounds the sweep at 6.4 attempts/clk/SM.
 MULWIDE_PER_CLK_SM = 32.0
 MULWIDE_PER_ATTEMPT = 5.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweeps_bits<64,4,4,float,512> launch (one
+# exchange interval, 3.36e8 attempts) from an ncu capture of this kernel version; None when the
+# kernel changed since (profiles/k_sweeps_bits_L64_R128_gaussian.md).
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.327872e6}
 
 
 def parse():
@@ -108,6 +112,26 @@ class ClockSampler:
 def temps():
     from paper_1508_06268_gb300 import inputs
     return inputs.geometric_temps(T_MIN, T_MAX, R)
+
+
+def shard_for_rank(rank):
+    """Realization-level sharding (weak scaling, no collective on the data path): rank r runs its
+    own disorder realization r with field seed 1 + r."""
+    return {"realization": rank, "field_seed": 1 + rank}
+
+
+def max_over_ranks(value, dist, device):
+    """The timed region's duration as the maximum over ranks (identity without a process group)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput: units processed by all ranks / slowest rank's time (units per ns)."""
+    return units_per_rank * world / (max_ms * 1e6)
 
 
 def cpu_baseline(budget_s=12.0):
@@ -274,8 +298,9 @@ def main():
         dist.init_process_group("nccl")
     layout = rf.LAYOUT_BITPACK if args.layout == "bitpack" else rf.LAYOUT_INT8
     T = temps()
-    real = rank
-    g = rf.Realization(L, T, J=J, h=H, field_kind=rf.FIELD_GAUSSIAN, field_seed=1 + real, seed=42,
+    sh = shard_for_rank(rank)
+    real = sh["realization"]
+    g = rf.Realization(L, T, J=J, h=H, field_kind=rf.FIELD_GAUSSIAN, field_seed=sh["field_seed"], seed=42,
                        realization=real, layout=layout)
     stream = torch.cuda.current_stream()
     measure_from = args.sweeps // EX // 2
@@ -306,13 +331,11 @@ def main():
     prof = g.profile_read()
     g.profile(False)
     launches = g.launch_count - launches0
-    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max = float(t.item())
+    dev_ms_max = max_over_ranks(dev_ms, dist, "cuda")
     attempts_rank = L ** 3 * R * args.sweeps * args.steps
-    value = attempts_rank * world / (dev_ms_max * 1e6)
+    value = aggregate_rate(attempts_rank, world, dev_ms_max)
 
     # dominant kernel: the sweep kernel (one launch per exchange interval)
     sweep_launch_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
@@ -322,7 +345,9 @@ def main():
     sm_mhz = clk["sm_mhz"] or 2070.0
     peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": SWEEP_TRAFFIC_BYTES.get("k_sweeps_bits") if layout == rf.LAYOUT_BITPACK else None,
+                "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
                 "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8",
                 "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
                               f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
