@@ -241,3 +241,89 @@ def test_invalid_configurations_rejected():
         g.adapt_temps(1, 10, 5, 2)  # capacity 3 cannot take 2 insertions
     g.sweep(0)
     assert g.get_state()["sweep"] == 0
+
+
+# ------------------------------------------------------------------ full configurations
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("layout", [BP, I8])
+def test_c2_full_run_matches_golden(layout):
+    """C2 in full: L=16 bimodal h=1.5, R=32, 10^4 sweeps, exchange every 5 (golden values written
+    by tests/golden/make_golden.py from the oracle)."""
+    import hashlib
+    gd = _golden("c2_bimodal_L16_R32.json")
+    c = gd["config"]
+    temps = inputs.geometric_temps(c["t_min"], c["t_max"], c["R"])
+    g = rf.Realization(c["L"], temps, h=c["h"], field_kind=BIM, field_seed=c["field_seed"], seed=c["seed"],
+                       realization=c["realization"], layout=layout)
+    g.run(c["sweeps"], c["exchange_every"], c["measure_from"])
+    st, ob = g.get_state(), g.observables()
+    assert st["t2r"].tolist() == gd["t2r"]
+    assert ob["att"].tolist() == gd["att"] and ob["acc"].tolist() == gd["acc"]
+    assert ob["n_meas"] == gd["n_meas"]
+    np.testing.assert_array_equal(ob["sums"], np.array(gd["obs_sums"]))
+    assert hashlib.sha256(st["spins"].astype(np.int8).tobytes()).hexdigest() == gd["spins_sha256"]
+
+
+def test_c4_full_size_gaussian_replay():
+    """L=64, R=128 Gaussian in the benchmark's launch configuration: one sweep from the oracle's
+    random start on both sides; decision mismatch fraction <= 1e-6."""
+    L, R = 64, 128
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    o = oracle.Oracle(L, temps, field_kind=oracle.FIELD_GAUSSIAN, field_seed=1, seed=42)
+    field = o.field()[0]
+    start = o.spins()
+    g = rf.Realization(L, temps, field_kind=EXP, field=field, seed=42, layout=BP)
+    g.set_state(spins=start)
+    o2 = oracle.Oracle(L, temps, field_kind=EXP, field=field, seed=42)
+    o2.set_spins(start)
+    o2.sweep(1)
+    g.sweep(1)
+    a, b = g.get_state()["spins"], o2.spins()
+    colour = brute.colour_of(L)
+    mism = int((a != b)[:, colour == 0].sum())
+    att = R * int((colour == 0).sum())
+    assert mism / att <= 1e-6, (mism, att)
+
+
+def test_c3_shaped_adaptation_invariants():
+    """L=32 Gaussian, R0=64 geometric in [1,5], 3 trials x 2000 sweeps (exchange every 10), a=2."""
+    L, R0, trials, a = 32, 64, 3, 2
+    temps = inputs.geometric_temps(1.0, 5.0, R0)
+    g = rf.Realization(L, temps, field_kind=GAU, field_seed=1, seed=42, layout=BP, R_capacity=R0 + trials * a)
+    T, rates = g.adapt_temps(trials, 2000, 10, a, return_rates=True)
+    assert g.R == 70 and len(T) == 70 and np.all(np.diff(T) > 0)
+    cur = list(temps)
+    for t in range(trials):
+        rt = rates[t, :len(cur) - 1]
+        assert np.all((rt >= 0) & (rt <= 1)) and rt.max() > 0
+        pick = [k for _, k in sorted((r, k) for k, r in enumerate(rt))][:a]
+        cur = sorted(cur + [0.5 * (cur[k] + cur[k + 1]) for k in pick])
+    np.testing.assert_array_equal(T, np.array(cur))
+    st = g.get_state()
+    assert st["sweep"] == 0 and st["xstep"] == 0 and st["t2r"].tolist() == list(range(70))
+
+
+@pytest.mark.parametrize("layout", [BP, I8])
+def test_checkpoint_resume_is_bit_identical(layout):
+    L, R = 16, 8
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 21)
+    ref = rf.Realization(L, temps, field_kind=EXP, field=field, layout=layout)
+    ref.run(30, 5, 0)
+    a = rf.Realization(L, temps, field_kind=EXP, field=field, layout=layout)
+    a.run(15, 5, 0)
+    ck = a.get_state()
+    b = rf.Realization(L, temps, field_kind=EXP, field=field, layout=layout)
+    b.set_state(spins=ck["spins"], t2r=ck["t2r"], sweep=ck["sweep"], xstep=ck["xstep"])
+    b.run(15, 5, 0)
+    fin, want = b.get_state(), ref.get_state()
+    np.testing.assert_array_equal(fin["spins"], want["spins"])
+    np.testing.assert_array_equal(fin["t2r"], want["t2r"])
+    assert fin["sweep"] == want["sweep"] == 30 and fin["xstep"] == want["xstep"] == 6
+    np.testing.assert_array_equal(a.observables()["acc"] + b.observables()["acc"], ref.observables()["acc"])
