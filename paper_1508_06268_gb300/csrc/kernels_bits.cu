@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "kernels_bits.cuh"
+#include "kernels_ws.cuh"
 #include "lattice.cuh"
 #include "sweep_bits.h"
 
@@ -44,6 +45,11 @@ KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
   RFIM_BITS_INSTANCE(8, 1, 1, 128)
   RFIM_BITS_INSTANCE(8, 1, 1, 512)
 #undef RFIM_BITS_INSTANCE
+  // warp-specialised variant (GT = 4, kWsThreads threads): selected by threads == kWsThreads
+  if (NT == kWsThreads && GT == kWsGT) {
+    if (L == 64 && S == 4) return bim ? (KernelFn)k_sweeps_ws<64, 4, true> : (KernelFn)k_sweeps_ws<64, 4, false>;
+    if (L == 64 && S == 2) return bim ? (KernelFn)k_sweeps_ws<64, 2, true> : (KernelFn)k_sweeps_ws<64, 2, false>;
+  }
   return nullptr;
 }
 
@@ -78,7 +84,8 @@ void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &
 }
 
 std::vector<std::string> plan_candidates(int32_t L) {
-  if (L == 64) return {"4,4,4,512", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "2,2,2,1024", "1,1,1,1024", "1,1,1,512"};
+  if (L == 64)
+    return {"4,4,4,512", "4,4,4,768", "2,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "2,2,2,1024", "1,1,1,1024"};
   if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512"};
   if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
   return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
@@ -108,7 +115,9 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   const char *o = t_plan_override ? t_plan_override : (!tuned.empty() ? tuned.c_str() : getenv("RFIM_BITS_PLAN"));
   if (o) {
     int s, g, gt, th;
-    if (sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4) {
+    // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
+    // ignored and the defaults stand
+    if (sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4 && kernel_for(L, s, gt, th, bimodal)) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;
     }
   }
@@ -120,7 +129,8 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
   }
-  p.smem = (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + (size_t)p.G * 128;
+  p.smem = p.threads == kWsThreads ? ws_smem(L, p.S, p.G)
+                                    : (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + (size_t)p.G * 128;
   if (p.smem > 227 * 1024) {
     if (err) *err = "bit-layout plan exceeds shared memory";
     return -1;
@@ -152,8 +162,8 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!rc) rc = grab((void **)&p.partM, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partFi, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partF, parts * 8, "partials");
-  if (!rc) rc = grab((void **)&p.counter, 4, "counter");
-  if (!rc && cudaMemset(p.counter, 0, 4) != cudaSuccess) rc = -3;
+  if (!rc) rc = grab((void **)&p.counter, 8, "counter");
+  if (!rc && cudaMemset(p.counter, 0, 8) != cudaSuccess) rc = -3;
   if (rc) {
     free_bits_plan(p);
     return rc;
@@ -197,6 +207,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.counter = plan.counter;
   xa.expected = 0;  // set by the kernel to its grid size
   xa.ctl = nullptr;
+  xa.err = plan.counter + 1;
   KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
   if (!fn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;

@@ -47,7 +47,8 @@ struct ExchArgs {
   double *partF;
   unsigned int *counter;
   unsigned int expected;
-  SlotCtl *ctl;  // batched launches only (else null)
+  SlotCtl *ctl;       // batched launches only (else null)
+  unsigned int *err;  // error word: bit 0 = a bounded device wait expired
 };
 
 __host__ __device__ __forceinline__ int64_t field4_index(int c, int64_t wq, int j, int64_t wpad) {
@@ -143,6 +144,132 @@ __device__ __forceinline__ T warp_reduce_sum(T x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;
 }
+
+// Fused exchange tail of an interval (Eq. 1 energies, then the last arrival takes exchange step
+// xa.j): slab partials of each replica from the lattice still in shared memory, an arrival count,
+// and for the last arrival the ordered reduction, E = -J B - F, exchange and measurement.
+template <int L, int S, bool BIM>
+__device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, int gact, int rank, int nsw,
+                                              const float4 *__restrict__ field4, const ExchArgs &xa) {
+  using Gm = BitsGeom<L>;
+  constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
+  constexpr int64_t WPAD = (W + 31) / 32 * 32;
+  extern __shared__ __align__(16) uint32_t sm[];
+  const int up_rank = (rank + 1) % S, dn_rank = (rank + S - 1) % S;
+  const int z0 = rank * PZ;
+  const uint32_t *sp = sm;
+  const int nt = blockDim.x, tid = threadIdx.x;
+
+  // ---- energy partials of this slab (Eq. 1): B over colour-0 words x their six neighbour words,
+  // M over all words, field term exact integer (bimodal) or error-free float sum (Sum2) -------
+  __shared__ long long red_i[3][32];
+  __shared__ double red_d[32];
+  __shared__ int last_cta;
+  const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+  for (int g = 0; g < gact; ++g) {
+    long long b = 0, m = 0, fi = 0;
+    float fs = 0.f, fe = 0.f;
+    for (int t = tid; t < 2 * WC; t += nt) {
+      const int c = t / WC, wl = t % WC;
+      const int zl = wl / P, iw = wl % P, z = z0 + zl;
+      const int64_t wq = (int64_t)z * P + iw;
+      const uint32_t self = sp[((size_t)g * 2 + c) * WC + wl];
+      m += 2 * __popc(self) - 32;
+      if (c == 0) {
+        uint32_t nb[6];
+        neighbour_words<L, S>(sp + ((size_t)g * 2 + 1) * WC, zl, iw, parity0_mask<L>(0, z, iw), up_rank, dn_rank, nb);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nb[d]);
+      }
+      if (BIM) {
+        fi += 32 - 2 * __popc(self ^ v.hbits[(int64_t)c * W + wq]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
+          const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float term = ((self >> (8 * k + j)) & 1u) ? hk[k] : -hk[k];
+            const float tsum = __fadd_rn(fs, term);
+            const float bp = __fsub_rn(tsum, fs);
+            fe = __fadd_rn(fe, __fadd_rn(__fsub_rn(fs, __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
+            fs = tsum;
+          }
+        }
+      }
+    }
+    b = warp_reduce_sum(b);
+    m = warp_reduce_sum(m);
+    fi = warp_reduce_sum(fi);
+    double fd = warp_reduce_sum((double)fs + (double)fe);
+    if (lane == 0) {
+      red_i[0][wid] = b;
+      red_i[1][wid] = m;
+      red_i[2][wid] = fi;
+      red_d[wid] = fd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long tb = 0, tm = 0, tf = 0;
+      double td = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        tb += red_i[0][w];
+        tm += red_i[1][w];
+        tf += red_i[2][w];
+        td += red_d[w];
+      }
+      const int64_t slot = (int64_t)(r0 + g) * S + rank;
+      xa.partB[slot] = tb;
+      xa.partM[slot] = tm;
+      xa.partFi[slot] = tf;
+      xa.partF[slot] = td;
+    }
+    __syncthreads();
+  }
+  sync_slabs<S>();  // peers may still read this CTA's halo planes
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(xa.counter, 1u);
+    last_cta = prev == xa.expected - 1;
+  }
+  __syncthreads();
+  if (!last_cta) return;
+  __threadfence();
+  for (int r = tid; r < v.R; r += nt) {
+    long long tb = 0, tm = 0, tf = 0;
+    double td = 0.0;
+    for (int q = 0; q < S; ++q) {
+      const int64_t slot = (int64_t)r * S + q;
+      tb += __ldcg(xa.partB + slot);
+      tm += __ldcg(xa.partM + slot);
+      tf += __ldcg(xa.partFi + slot);
+      td += __ldcg(xa.partF + slot);
+    }
+    const double F = BIM ? xa.h * (double)tf : td;
+    v.E[r] = -xa.J * (double)tb - F;
+    v.M[r] = tm;
+  }
+  __syncthreads();
+  exchange_and_measure(v, xa.j, xa.measure_from);
+  if (tid == 0) {
+    *xa.counter = 0u;
+    if (xa.ctl) {
+      SlotCtl *c = xa.ctl;
+      c->sweep0 += (uint32_t)nsw;
+      c->j += 1u;
+      c->intervals_left -= 1;
+      if (c->intervals_left == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        c->done_ns = t;
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
 
 // One exchange interval of replicas [r0, r0 + gact) of realization v, slab `rank` of S: load into
 // shared memory, nsw sweeps, write back, and (xa.enabled) the energy partials and the exchange
@@ -262,116 +389,7 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl] = sp[t];
   }
-  if (!xa.enabled) return;
-
-  // ---- energy partials of this slab (Eq. 1): B over colour-0 words x their six neighbour words,
-  // M over all words, field term exact integer (bimodal) or error-free float sum (Sum2) -------
-  __shared__ long long red_i[3][32];
-  __shared__ double red_d[32];
-  __shared__ int last_cta;
-  const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
-  for (int g = 0; g < gact; ++g) {
-    long long b = 0, m = 0, fi = 0;
-    float fs = 0.f, fe = 0.f;
-    for (int t = tid; t < 2 * WC; t += nt) {
-      const int c = t / WC, wl = t % WC;
-      const int zl = wl / P, iw = wl % P, z = z0 + zl;
-      const int64_t wq = (int64_t)z * P + iw;
-      const uint32_t self = sp[((size_t)g * 2 + c) * WC + wl];
-      m += 2 * __popc(self) - 32;
-      if (c == 0) {
-        uint32_t nb[6];
-        neighbour_words<L, S>(sp + ((size_t)g * 2 + 1) * WC, zl, iw, parity0_mask<L>(0, z, iw), up_rank, dn_rank, nb);
-#pragma unroll
-        for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nb[d]);
-      }
-      if (BIM) {
-        fi += 32 - 2 * __popc(self ^ v.hbits[(int64_t)c * W + wq]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
-          const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float term = ((self >> (8 * k + j)) & 1u) ? hk[k] : -hk[k];
-            const float tsum = __fadd_rn(fs, term);
-            const float bp = __fsub_rn(tsum, fs);
-            fe = __fadd_rn(fe, __fadd_rn(__fsub_rn(fs, __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
-            fs = tsum;
-          }
-        }
-      }
-    }
-    b = warp_reduce_sum(b);
-    m = warp_reduce_sum(m);
-    fi = warp_reduce_sum(fi);
-    double fd = warp_reduce_sum((double)fs + (double)fe);
-    if (lane == 0) {
-      red_i[0][wid] = b;
-      red_i[1][wid] = m;
-      red_i[2][wid] = fi;
-      red_d[wid] = fd;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      long long tb = 0, tm = 0, tf = 0;
-      double td = 0.0;
-      for (int w = 0; w < nw; ++w) {
-        tb += red_i[0][w];
-        tm += red_i[1][w];
-        tf += red_i[2][w];
-        td += red_d[w];
-      }
-      const int64_t slot = (int64_t)(r0 + g) * S + rank;
-      xa.partB[slot] = tb;
-      xa.partM[slot] = tm;
-      xa.partFi[slot] = tf;
-      xa.partF[slot] = td;
-    }
-    __syncthreads();
-  }
-  sync_slabs<S>();  // peers may still read this CTA's halo planes
-  if (tid == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(xa.counter, 1u);
-    last_cta = prev == xa.expected - 1;
-  }
-  __syncthreads();
-  if (!last_cta) return;
-  __threadfence();
-  for (int r = tid; r < v.R; r += nt) {
-    long long tb = 0, tm = 0, tf = 0;
-    double td = 0.0;
-    for (int q = 0; q < S; ++q) {
-      const int64_t slot = (int64_t)r * S + q;
-      tb += __ldcg(xa.partB + slot);
-      tm += __ldcg(xa.partM + slot);
-      tf += __ldcg(xa.partFi + slot);
-      td += __ldcg(xa.partF + slot);
-    }
-    const double F = BIM ? xa.h * (double)tf : td;
-    v.E[r] = -xa.J * (double)tb - F;
-    v.M[r] = tm;
-  }
-  __syncthreads();
-  exchange_and_measure(v, xa.j, xa.measure_from);
-  if (tid == 0) {
-    *xa.counter = 0u;
-    if (xa.ctl) {
-      SlotCtl *c = xa.ctl;
-      c->sweep0 += (uint32_t)nsw;
-      c->j += 1u;
-      c->intervals_left -= 1;
-      if (c->intervals_left == 0) {
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        c->done_ns = t;
-      }
-      __threadfence();
-    }
-  }
-  __syncthreads();
+  if (xa.enabled) interval_tail<L, S, BIM>(v, G, r0, gact, rank, nsw, field4, xa);
 }
 
 template <int L, int S, int GT, bool BIM, int NT>

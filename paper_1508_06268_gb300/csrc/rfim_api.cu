@@ -186,6 +186,18 @@ int reset_state(rfim_ctx *c, uint32_t stage) {
   return RFIM_OK;
 }
 
+// Bounded device waits that expired (bit-layout kernels) surface as RFIM_ETIMEOUT; the word is
+// cleared once reported.  Synchronises the stream.
+int check_device_error(rfim_ctx *c) {
+  if (c->layout != RFIM_LAYOUT_BITPACK || !c->plan.counter) return RFIM_OK;
+  unsigned int word = 0;
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(&word, c->plan.counter + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  if (!word) return RFIM_OK;
+  CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.counter + 1, 0, 4, c->stream));
+  return fail(c, RFIM_ETIMEOUT, "a bounded device wait expired (error word %u); results of that launch are invalid", word);
+}
+
 int do_sweeps(rfim_ctx *c, int64_t n) {
   if (n <= 0) return RFIM_OK;
   RealView v = view_of(c);
@@ -459,6 +471,7 @@ int rfim_adapt_temps(rfim_ctx *ctx, int32_t n_trials, int64_t sweeps_per_trial, 
 int rfim_observables(rfim_ctx *ctx, rfim_obs *out) {
   if (!ctx || !out) return RFIM_EINVAL;
   rfim_ctx *c = ctx;
+  if (int rc = check_device_error(c)) return rc;
   const int32_t R = c->R;
   std::vector<double> obs((size_t)R * 5);
   std::vector<uint64_t> att(R), acc(R);
@@ -483,6 +496,7 @@ int rfim_observables(rfim_ctx *ctx, rfim_obs *out) {
 int rfim_get_state(rfim_ctx *ctx, int8_t *spins, int32_t *t2r, double *E, int64_t *sweep, int64_t *xstep) {
   if (!ctx) return RFIM_EINVAL;
   rfim_ctx *c = ctx;
+  if (int rc = check_device_error(c)) return rc;
   const size_t RN = (size_t)c->R * c->N;
   RealView v = view_of(c);
   if (spins) {

@@ -327,3 +327,20 @@ def test_checkpoint_resume_is_bit_identical(layout):
     np.testing.assert_array_equal(fin["t2r"], want["t2r"])
     assert fin["sweep"] == want["sweep"] == 30 and fin["xstep"] == want["xstep"] == 6
     np.testing.assert_array_equal(a.observables()["acc"] + b.observables()["acc"], ref.observables()["acc"])
+
+
+@pytest.mark.parametrize("kind", [BIM, GAU])
+def test_warp_specialised_variant_matches(kind, monkeypatch):
+    """The producer/consumer variant (launch shape 4,4,4,768) takes the same decisions."""
+    L, R = 64, 8
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    ref = rf.Realization(L, temps, field_kind=kind, h=1.2, layout=BP)
+    monkeypatch.setenv("RFIM_BITS_PLAN", "4,4,4,768")
+    ws = rf.Realization(L, temps, field_kind=kind, h=1.2, layout=BP)
+    monkeypatch.delenv("RFIM_BITS_PLAN")
+    for g in (ref, ws):
+        g.run(20, 5, 0)
+    a, b = ref.get_state(), ws.get_state()
+    np.testing.assert_array_equal(a["spins"], b["spins"])
+    np.testing.assert_array_equal(a["t2r"], b["t2r"])
+    np.testing.assert_array_equal(ref.observables()["sums"], ws.observables()["sums"])
