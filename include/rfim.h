@@ -252,6 +252,11 @@ int rfim_tune(int32_t L, int32_t R, int32_t field_kind, char *plan_out, int32_t 
    Returns the number of mismatching sites (0 = pass) or -1 for an unsupported L. */
 int rfim_selftest_bits(int32_t L, uint32_t seed);
 
+/* Host-only self-check of the partition used by the grid-wide bit-layout kernel (replica groups
+   of 4 x z planes spread over P CTAs): unique owners, pieces tiling every CTA's range.  Returns
+   the number of violations (0 = pass) or -1 for invalid arguments. */
+int rfim_selftest_grid(int32_t L, int32_t R, int32_t P);
+
 #ifdef __cplusplus
 }
 #endif

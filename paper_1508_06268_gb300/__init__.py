@@ -100,6 +100,7 @@ def load():
             L.rfim_server_last_error.argtypes = [P]
             L.rfim_server_last_error.restype = C.c_char_p
             L.rfim_exchange_noalloc.argtypes = [C.POINTER(ExchangeBuffers), u32, i64, P]
+            L.rfim_selftest_grid.argtypes = [i32, i32, i32]
             L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
@@ -108,7 +109,7 @@ def load():
                          "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
                          "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
                          "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
-                         "rfim_exchange_noalloc", "rfim_tune"):
+                         "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -141,6 +142,10 @@ def tune(L: int, R: int, field_kind: int = FIELD_GAUSSIAN):
     if rc != OK:
         raise RfimError(rc, lib.rfim_last_error(None).decode())
     return buf.value.decode(), rate.value
+
+
+def selftest_grid(L: int, R: int, P: int) -> int:
+    return load().rfim_selftest_grid(L, R, P)
 
 
 def selftest_bits(L: int, seed: int = 1) -> int:

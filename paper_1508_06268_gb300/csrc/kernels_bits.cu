@@ -1,5 +1,6 @@
 // Launch plan, dispatch and helpers of the bit-layout sweep kernel (kernels_bits.cuh).
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -9,6 +10,7 @@
 
 #include "kernels_bits.cuh"
 #include "kernels_ws.cuh"
+#include "kernels_grid.cuh"
 #include "lattice.cuh"
 #include "sweep_bits.h"
 
@@ -53,7 +55,47 @@ KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
   return nullptr;
 }
 
-int words_per_cta(int L, int S) { return (L / S) * (L * L / 64); }
+int words_per_cta(int L, int S) { return L <= 0 || S <= 0 ? 0 : (L / S) * (L * L / 64); }
+
+using GridFn = void (*)(RealView, GridArgs, uint32_t, int32_t, const float4 *, ExchArgs);
+
+GridFn grid_kernel_for(int L, bool bim) {
+  if (L == 64) return bim ? (GridFn)k_sweeps_grid<64, true> : (GridFn)k_sweeps_grid<64, false>;
+  if (L == 32) return bim ? (GridFn)k_sweeps_grid<32, true> : (GridFn)k_sweeps_grid<32, false>;
+  return nullptr;
+}
+
+constexpr size_t kGridMinSmem = 116 * 1024;  // more than half an SM's shared memory: one CTA per SM
+
+// Partition of the current R over the CTAs of a grid-wide launch.
+GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
+  GridArgs ga{};
+  ga.gp.L = p.L;
+  ga.gp.NG = (R + kGridGroup - 1) / kGridGroup;
+  ga.gp.U = (int64_t)ga.gp.NG * p.L;
+  int64_t P = std::min<int64_t>(sms, ga.gp.U / 3);
+  if (P < 1) P = 1;
+  ga.gp.P = (int32_t)P;
+  int maxu = 0, slots = 0;
+  for (int k = 0; k < ga.gp.P; ++k) maxu = std::max<int>(maxu, (int)(grid_begin(ga.gp, k + 1) - grid_begin(ga.gp, k)));
+  for (int g = 0; g < ga.gp.NG; ++g)
+    slots = std::max(slots, grid_owner(ga.gp, (int64_t)g * p.L + p.L - 1) - grid_owner(ga.gp, (int64_t)g * p.L) + 1);
+  ga.max_units = maxu;
+  ga.slots = slots;
+  ga.prog = p.prog;
+  ga.partB = p.gpartB;
+  ga.partM = p.gpartM;
+  ga.partFi = p.gpartFi;
+  ga.partF = p.gpartF;
+  return ga;
+}
+
+size_t grid_smem(int L, int max_units) {
+  const size_t PW = (size_t)L * L / 64;
+  const size_t need = (size_t)max_units * kGridGroup * 2 * PW * 4 + (size_t)kGridMaxPieces * 2 * kGridGroup * PW * 4 +
+                      (size_t)kGridMaxPieces * kGridGroup * 128;
+  return std::max(need, kGridMinSmem);
+}
 
 __global__ void k_build_field4(RealView v, float4 *field4, int64_t wpad) {
   const int64_t half = (int64_t)v.N / 2, W = half / 32;
@@ -85,8 +127,8 @@ void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &
 
 std::vector<std::string> plan_candidates(int32_t L) {
   if (L == 64)
-    return {"4,4,4,512", "4,4,4,768", "2,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "2,2,2,1024", "1,1,1,1024"};
-  if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512"};
+    return {"4,4,4,512", "0,4,4,512", "0,4,4,448", "4,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
+  if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512"};
   if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
   return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
 }
@@ -95,8 +137,17 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   BitsPlan p;
   p.L = L;
   p.Rcap = Rcap;
+  int sms_dev = 0;
+  cudaDeviceGetAttribute(&sms_dev, cudaDevAttrMultiProcessorCount, 0);
   if (L == 64) {
-    p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
+    // clusters of 4 z slabs x 4 replicas, unless they would leave more than a fifth of the SMs
+    // idle (e.g. R = 70 after adaptation: 72 CTAs); then the grid-wide plan covers every SM
+    const int cluster_ctas = 4 * ((Rcap + 3) / 4);
+    if (sms_dev > 0 && cluster_ctas < (4 * sms_dev) / 5) {
+      p.S = 0; p.G = 4; p.GT = 4; p.threads = 512;
+    } else {
+      p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
+    }
   } else if (L == 32) {
     p.S = 1; p.G = 1; p.GT = 1; p.threads = 512;
   } else if (L == 16) {
@@ -117,27 +168,50 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     int s, g, gt, th;
     // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
     // ignored and the defaults stand
-    if (sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4 && kernel_for(L, s, gt, th, bimodal)) {
+    const bool named = sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4;
+    const bool exists = named && (s == 0 ? (gt == kGridGroup && th >= 256 && th <= 512 && grid_kernel_for(L, bimodal))
+                                         : kernel_for(L, s, gt, th, bimodal) != nullptr);
+    if (exists) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;
     }
   }
   if (p.G > Rcap) p.G = Rcap;
   if (p.GT > p.G) p.GT = 1;
   if (p.G % p.GT) p.G = (p.G / p.GT) * p.GT;
-  KernelFn fn = kernel_for(L, p.S, p.GT, p.threads, bimodal);
-  if (!fn) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal);
+  GridFn gfn = p.S == 0 && p.GT == kGridGroup && p.threads >= 256 && p.threads <= 512 ? grid_kernel_for(L, bimodal) : nullptr;
+  if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
   }
-  p.smem = p.threads == kWsThreads ? ws_smem(L, p.S, p.G)
-                                    : (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + (size_t)p.G * 128;
+  if (gfn) {
+    p.G = kGridGroup;
+    p.sms = sms;
+    // largest partition over every R the context can reach
+    int maxu = 0;
+    for (int32_t R = 2; R <= Rcap; ++R) {
+      BitsPlan q = p;
+      maxu = std::max(maxu, grid_args(q, R, sms).max_units);
+    }
+    if (maxu > 255) {
+      if (err) *err = "grid plan: too many planes per CTA";
+      return -1;
+    }
+    p.smem = grid_smem(L, maxu);
+  }
+  if (!gfn)
+    p.smem = p.threads == kWsThreads ? ws_smem(L, p.S, p.G)
+                                      : (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + (size_t)p.G * 128;
   if (p.smem > 227 * 1024) {
     if (err) *err = "bit-layout plan exceeds shared memory";
     return -1;
   }
-  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  const void *fptr = gfn ? (const void *)gfn : (const void *)fn;
+  cudaError_t e = cudaFuncSetAttribute(fptr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e == cudaSuccess && p.S > 1)
-    e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(fptr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) {
     if (err) *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return -3;  // RFIM_ECUDA
@@ -163,6 +237,14 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!rc) rc = grab((void **)&p.partFi, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partF, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.counter, 8, "counter");
+  if (!rc && gfn) {
+    const size_t gslots = (size_t)Rcap * (L + 1);
+    rc = grab((void **)&p.gpartB, gslots * 8, "grid partials");
+    if (!rc) rc = grab((void **)&p.gpartM, gslots * 8, "grid partials");
+    if (!rc) rc = grab((void **)&p.gpartFi, gslots * 8, "grid partials");
+    if (!rc) rc = grab((void **)&p.gpartF, gslots * 8, "grid partials");
+    if (!rc) rc = grab((void **)&p.prog, (size_t)std::max(sms, 1) * 4, "progress words");
+  }
   if (!rc && cudaMemset(p.counter, 0, 8) != cudaSuccess) rc = -3;
   if (rc) {
     free_bits_plan(p);
@@ -175,13 +257,17 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
 bool bits_plan_fits(const BitsPlan &plan, int32_t R) { return R <= plan.Rcap; }
 
 void free_bits_plan(BitsPlan &plan) {
-  void *ptrs[] = {plan.field4, plan.partB, plan.partM, plan.partFi, plan.partF, plan.counter};
+  void *ptrs[] = {plan.field4, plan.partB, plan.partM, plan.partFi, plan.partF, plan.counter,
+                  plan.gpartB,  plan.gpartM, plan.gpartFi, plan.gpartF, plan.prog};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   plan.field4 = nullptr;
   plan.partB = plan.partM = plan.partFi = nullptr;
   plan.partF = nullptr;
   plan.counter = nullptr;
+  plan.gpartB = plan.gpartM = plan.gpartFi = nullptr;
+  plan.gpartF = nullptr;
+  plan.prog = nullptr;
 }
 
 cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
@@ -208,6 +294,24 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.expected = 0;  // set by the kernel to its grid size
   xa.ctl = nullptr;
   xa.err = plan.counter + 1;
+  if (plan.S == 0) {
+    GridFn gfn = grid_kernel_for(plan.L, v.kind == kBimodal);
+    if (!gfn) return cudaErrorInvalidConfiguration;
+    GridArgs ga = grid_args(plan, v.R, plan.sms);
+    cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ga.gp.P);
+    cfg.blockDim = dim3((unsigned)plan.threads);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gfn, v, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
+  }
   KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
   if (!fn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;
@@ -293,4 +397,33 @@ extern "C" int rfim_selftest_bits(int32_t L, uint32_t seed) {
     case 64: return selftest_bits_L<64>(seed);
     default: return -1;
   }
+}
+
+// Host self-check of the grid-wide partition: every unit has exactly one owner consistent with
+// the CTA ranges, pieces tile each range inside single groups, at most kGridMaxPieces per CTA.
+extern "C" int rfim_selftest_grid(int32_t L, int32_t R, int32_t P) {
+  using namespace rfim;
+  if (L < 2 || R < 2 || P < 1) return -1;
+  GridPart gp{};
+  gp.L = L;
+  gp.NG = (R + kGridGroup - 1) / kGridGroup;
+  gp.U = (int64_t)gp.NG * L;
+  gp.P = P;
+  int bad = 0;
+  for (int k = 0; k < P; ++k) {
+    const int64_t a = grid_begin(gp, k), b = grid_begin(gp, k + 1);
+    for (int64_t u = a; u < b; ++u) bad += grid_owner(gp, u) != k;
+    Piece pc[kGridMaxPieces];
+    const int np = grid_pieces(gp, k, pc);
+    int64_t covered = 0;
+    for (int p = 0; p < np; ++p) {
+      const int64_t u0 = (int64_t)pc[p].g * L + pc[p].z0;
+      bad += u0 != a + pc[p].lu0;
+      bad += pc[p].z0 + pc[p].n > L;
+      bad += grid_slab_of(gp, k, pc[p].g) < 0;
+      covered += pc[p].n;
+    }
+    bad += covered != b - a;
+  }
+  return bad;
 }

@@ -1,0 +1,338 @@
+// Grid-wide bit-layout sweep: one cooperative launch with one CTA per SM covers every SM, whatever
+// the replica count.  Same arithmetic and decisions as kernels_bits.cuh.
+//
+// The realization's (4-replica group, z plane) units are split evenly over the CTAs
+// (grid_partition.cuh); each CTA keeps its planes of both colours in shared memory for the whole
+// exchange interval.  The z neighbours of a piece's end planes live in other CTAs: after every
+// half-sweep a CTA writes the end planes it just updated to the global lattice and releases its
+// progress word; before touching its own end planes in the next half-sweep it acquires its
+// neighbours' progress words and reads their end planes (L2).  Each half-sweep first processes a
+// whole round of interior planes, so that wait is normally already satisfied.  Waits are bounded
+// (expiry sets the kernel's error word and every later wait returns at once); the kernel always
+// terminates.
+#pragma once
+#include <cstdint>
+
+#include "grid_partition.cuh"
+#include "kernels_bits.cuh"
+
+namespace rfim {
+
+constexpr unsigned kGridSpinLimit = 1u << 22;
+
+struct GridArgs {
+  GridPart gp;
+  unsigned int *prog;  // [P] half-sweeps completed by each CTA in this launch (zeroed before it)
+  int32_t max_units;   // units of the largest CTA (shared-memory sizing)
+  int32_t slots;       // partial-sum slots per replica (CTAs sharing one group, at most)
+  long long *partB, *partM, *partFi;  // [Rcap][slots]
+  double *partF;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait for prog[k] >= need; false on expiry (which is recorded) or an earlier expiry.
+__device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned need, unsigned *err) {
+  for (unsigned it = 0; it < kGridSpinLimit; ++it) {
+    if (ld_acquire_u32(prog + k) >= need) return true;
+    if (*(volatile unsigned *)err) return false;
+    __nanosleep(64);
+  }
+  atomicOr(err, 2u);
+  return false;
+}
+
+template <int L, bool BIM>
+__global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
+                                                        const float4 *__restrict__ field4, ExchArgs xa) {
+  constexpr int PW = L * L / 64, W = L * L * L / 64;
+  constexpr int64_t WPAD = (W + 31) / 32 * 32;
+  constexpr int GG = kGridGroup;
+  extern __shared__ __align__(16) uint32_t sm[];
+  const int k = blockIdx.x, nt = blockDim.x, tid = threadIdx.x;
+  __shared__ Piece pc[kGridMaxPieces];
+  __shared__ int np_s, nu_s, nb_s;
+  __shared__ int8_t plane_piece[256];
+  __shared__ uint8_t order[256];  // local planes: interior first, then piece end planes
+  if (tid == 0) {
+    Piece tmp[kGridMaxPieces];
+    const int np = grid_pieces(ga.gp, k, tmp);
+    int nu = 0;
+    for (int p = 0; p < np; ++p) {
+      pc[p] = tmp[p];
+      for (int i = 0; i < tmp[p].n; ++i) plane_piece[tmp[p].lu0 + i] = (int8_t)p;
+      nu += tmp[p].n;
+    }
+    int o = 0;
+    for (int p = 0; p < np; ++p)
+      for (int i = 1; i + 1 < tmp[p].n; ++i) order[o++] = (uint8_t)(tmp[p].lu0 + i);
+    const int nint = o;
+    for (int p = 0; p < np; ++p) {
+      order[o++] = (uint8_t)tmp[p].lu0;
+      if (tmp[p].n > 1) order[o++] = (uint8_t)(tmp[p].lu0 + tmp[p].n - 1);
+    }
+    np_s = np;
+    nu_s = nu;
+    nb_s = nu - nint;
+  }
+  __syncthreads();
+  const int np = np_s, nu = nu_s, nb = nb_s;
+  uint32_t *lat = sm;                                          // [max_units][GG][2][PW]
+  uint32_t *halo = lat + (size_t)ga.max_units * GG * 2 * PW;  // [pieces][2][GG][PW] (other colour)
+  uint32_t *tab = halo + (size_t)kGridMaxPieces * 2 * GG * PW;  // [pieces][GG] x 128 bytes
+  auto lat_at = [&](int lu, int gg, int c) { return lat + ((size_t)(lu * GG + gg) * 2 + c) * PW; };
+  auto halo_at = [&](int p, int side, int gg) { return halo + ((size_t)(p * 2 + side) * GG + gg) * PW; };
+  auto gact_of = [&](int p) { return min(GG, v.R - pc[p].g * GG); };
+
+  for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
+    const int lu = t / (GG * 2 * PW), rem = t % (GG * 2 * PW), gg = rem / (2 * PW), c = (rem / PW) & 1, w = rem % PW;
+    const Piece &q = pc[plane_piece[lu]];
+    const int r = q.g * GG + gg, z = q.z0 + (lu - q.lu0);
+    lat[t] = r < v.R ? v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] : 0u;
+  }
+  for (int t = tid; t < np * GG * 32; t += nt) {
+    const int p = t / (GG * 32), gg = (t / 32) % GG, i = t % 32;
+    const int r = min(pc[p].g * GG + gg, v.R - 1);
+    if (BIM) {
+      tab[t] = v.thr[(int64_t)v.r2t[r] * 32 + i];
+    } else if (i < 16) {
+      const float b = v.b2l[v.r2t[r]];
+      reinterpret_cast<float2 *>(tab)[(p * GG + gg) * 16 + i] = make_float2(v.gjn[i & 7], (i >> 3) ? b : -b);
+    }
+  }
+  __syncthreads();
+
+  const int items = nu * PW;
+  const int phase_a = ((nu - nb) * PW / nt) * nt;  // whole rounds of interior planes
+  unsigned *err = xa.err;
+
+  // Loads the other colour's end planes of every piece's z neighbours once they have finished
+  // `need` half-sweeps.
+  auto fetch_halos = [&](int other, unsigned need) {
+    if (tid == 0) {
+      for (int p = 0; p < np; ++p) {
+        const int64_t base = (int64_t)pc[p].g * L;
+        const int klo = grid_owner(ga.gp, base + (pc[p].z0 + L - 1) % L);
+        const int khi = grid_owner(ga.gp, base + (pc[p].z0 + pc[p].n) % L);
+        grid_wait(ga.prog, klo, need, err);
+        grid_wait(ga.prog, khi, need, err);
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < np * 2 * GG * PW; t += nt) {
+      const int p = t / (2 * GG * PW), side = (t / (GG * PW)) & 1, gg = (t / PW) % GG, w = t % PW;
+      const int r = min(pc[p].g * GG + gg, v.R - 1);
+      const int z = side ? (pc[p].z0 + pc[p].n) % L : (pc[p].z0 + L - 1) % L;
+      halo[t] = __ldcg(v.bits + ((int64_t)r * 2 + other) * W + (int64_t)z * PW + w);
+    }
+    __syncthreads();
+  };
+
+  // z-neighbour words (other colour) of local plane lu, word w, replica gg
+  auto zn = [&](int lu, int w, int gg, int other, uint32_t &up, uint32_t &dn) {
+    const int p = plane_piece[lu];
+    const int pl = lu - pc[p].lu0;
+    up = pl + 1 < pc[p].n ? lat_at(lu + 1, gg, other)[w] : halo_at(p, 1, gg)[w];
+    dn = pl > 0 ? lat_at(lu - 1, gg, other)[w] : halo_at(p, 0, gg)[w];
+  };
+
+  for (int h = 0; h < 2 * nsw; ++h) {
+    const int c = h & 1, other = c ^ 1;
+    const uint32_t sweep = sweep0 + (uint32_t)(h >> 1);
+    const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)c);
+    auto process = [&](int i0, int i1) {
+#pragma unroll 1
+      for (int it = i0 + tid; it < i1; it += nt) {
+        const int lu = order[it / PW], w = it % PW;
+        const int p = plane_piece[lu];
+        const int z = pc[p].z0 + (lu - pc[p].lu0);
+        const int64_t wq = (int64_t)z * PW + w;
+        const int gact = gact_of(p);
+        float4 hh4[8];
+        if (!BIM) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
+        }
+        const uint32_t p0 = parity0_mask<L>(c, z, w);
+        PairSlices ps[GG];
+        uint32_t sf[GG], flip[GG], fk[GG][4];
+        const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+#pragma unroll
+        for (int gg = 0; gg < GG; ++gg) {
+          const int g = min(gg, gact - 1);
+          const uint32_t *O = lat_at(lu, g, other);
+          uint32_t nbw[6], c0, c1, c2;
+          nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], p0, nbw[0], nbw[1], nbw[2], nbw[3]);
+          zn(lu, w, g, other, nbw[4], nbw[5]);
+          count6(nbw[0], nbw[1], nbw[2], nbw[3], nbw[4], nbw[5], c0, c1, c2);
+          sf[gg] = lat_at(lu, g, c)[w];
+          ps[gg] = make_pairs(c0, c1, c2, sf[gg], fb);
+          flip[gg] = 0u;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) fk[gg][q] = 0u;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = 7 - jj;
+#pragma unroll
+          for (int gg = 0; gg < GG; ++gg) {
+            const int g = min(gg, gact - 1);
+            const int r = pc[p].g * GG + g;
+            const Words4 wd = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)r, sweep, tag);
+            const uint32_t acc = block_offsets<BIM>(ps[gg], j);
+            const char *tb = reinterpret_cast<const char *>(tab) + (p * GG + g) * 128;
+            const float hk[4] = {hh4[j].x, hh4[j].y, hh4[j].z, hh4[j].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t off = (acc >> (8 * q)) & (BIM ? 0x7Cu : 0x78u);
+              if (BIM) {
+                if (accept_table(wd.w[q], *reinterpret_cast<const uint32_t *>(tb + off))) flip[gg] |= 1u << (8 * q + j);
+              } else {
+                const float2 e = *reinterpret_cast<const float2 *>(tb + off);
+                fk[gg][q] = __funnelshift_l(accept_float_sign(wd.w[q], e.x, hk[q], e.y), fk[gg][q], 1);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int gg = 0; gg < GG; ++gg) {
+          if (gg >= gact) continue;
+          if (!BIM) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
+          lat_at(lu, gg, c)[w] = sf[gg] ^ flip[gg];
+        }
+      }
+    };
+    process(0, phase_a);
+    fetch_halos(other, (unsigned)h);
+    process(phase_a, items);
+    __syncthreads();
+    // publish this half-sweep's end planes (colour c), then the progress word
+    for (int t = tid; t < np * 2 * GG * PW; t += nt) {
+      const int p = t / (2 * GG * PW), side = (t / (GG * PW)) & 1, gg = (t / PW) % GG, w = t % PW;
+      if (gg >= gact_of(p) || (side && pc[p].n == 1)) continue;
+      const int lu = side ? pc[p].lu0 + pc[p].n - 1 : pc[p].lu0;
+      const int r = pc[p].g * GG + gg, z = pc[p].z0 + (lu - pc[p].lu0);
+      v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = lat_at(lu, gg, c)[w];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release_u32(ga.prog + k, (unsigned)(h + 1));
+  }
+
+  for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
+    const int lu = t / (GG * 2 * PW), rem = t % (GG * 2 * PW), gg = rem / (2 * PW), c = (rem / PW) & 1, w = rem % PW;
+    const Piece &q = pc[plane_piece[lu]];
+    const int r = q.g * GG + gg, z = q.z0 + (lu - q.lu0);
+    if (r < v.R) v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = lat[t];
+  }
+  if (!xa.enabled) return;
+
+  // ---- energy partials (Eq. 1) per (replica, piece), then the exchange tail ----------------
+  fetch_halos(1, (unsigned)(2 * nsw));  // final colour-1 end planes of the neighbours
+  __shared__ long long red_i[3][32];
+  __shared__ double red_d[32];
+  __shared__ int last_cta;
+  const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+  for (int p = 0; p < np; ++p) {
+    const int gact = gact_of(p);
+    for (int gg = 0; gg < gact; ++gg) {
+      long long b = 0, m = 0, fi = 0;
+      float fs = 0.f, fe = 0.f;
+      for (int t = tid; t < pc[p].n * 2 * PW; t += nt) {
+        const int c = t / (pc[p].n * PW), rem = t % (pc[p].n * PW), pl = rem / PW, w = rem % PW;
+        const int lu = pc[p].lu0 + pl, z = pc[p].z0 + pl;
+        const int64_t wq = (int64_t)z * PW + w;
+        const uint32_t self = lat_at(lu, gg, c)[w];
+        m += 2 * __popc(self) - 32;
+        if (c == 0) {
+          const uint32_t *O = lat_at(lu, gg, 1);
+          uint32_t nbw[6];
+          nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], parity0_mask<L>(0, z, w), nbw[0], nbw[1], nbw[2], nbw[3]);
+          zn(lu, w, gg, 1, nbw[4], nbw[5]);
+#pragma unroll
+          for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nbw[d]);
+        }
+        if (BIM) {
+          fi += 32 - 2 * __popc(self ^ v.hbits[(int64_t)c * W + wq]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
+            const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float term = ((self >> (8 * q + j)) & 1u) ? hk[q] : -hk[q];
+              const float tsum = __fadd_rn(fs, term);
+              const float bp = __fsub_rn(tsum, fs);
+              fe = __fadd_rn(fe, __fadd_rn(__fsub_rn(fs, __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
+              fs = tsum;
+            }
+          }
+        }
+      }
+      b = warp_reduce_sum(b);
+      m = warp_reduce_sum(m);
+      fi = warp_reduce_sum(fi);
+      double fd = warp_reduce_sum((double)fs + (double)fe);
+      if (lane == 0) {
+        red_i[0][wid] = b;
+        red_i[1][wid] = m;
+        red_i[2][wid] = fi;
+        red_d[wid] = fd;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        long long tb = 0, tm = 0, tf = 0;
+        double td = 0.0;
+        for (int w = 0; w < nw; ++w) {
+          tb += red_i[0][w];
+          tm += red_i[1][w];
+          tf += red_i[2][w];
+          td += red_d[w];
+        }
+        const int64_t slot = (int64_t)(pc[p].g * GG + gg) * ga.slots + grid_slab_of(ga.gp, k, pc[p].g);
+        ga.partB[slot] = tb;
+        ga.partM[slot] = tm;
+        ga.partFi[slot] = tf;
+        ga.partF[slot] = td;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    __threadfence();
+    last_cta = atomicAdd(xa.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_cta) return;
+  __threadfence();
+  for (int r = tid; r < v.R; r += nt) {
+    const int g = r / GG;
+    const int nslab = grid_owner(ga.gp, (int64_t)g * L + L - 1) - grid_owner(ga.gp, (int64_t)g * L) + 1;
+    long long tb = 0, tm = 0, tf = 0;
+    double td = 0.0;
+    for (int q = 0; q < nslab; ++q) {
+      const int64_t slot = (int64_t)r * ga.slots + q;
+      tb += __ldcg(ga.partB + slot);
+      tm += __ldcg(ga.partM + slot);
+      tf += __ldcg(ga.partFi + slot);
+      td += __ldcg(ga.partF + slot);
+    }
+    const double F = BIM ? xa.h * (double)tf : td;
+    v.E[r] = -xa.J * (double)tb - F;
+    v.M[r] = tm;
+  }
+  __syncthreads();
+  exchange_and_measure(v, xa.j, xa.measure_from);
+  if (tid == 0) *xa.counter = 0u;
+}
+
+}  // namespace rfim

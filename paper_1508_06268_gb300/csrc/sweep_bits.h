@@ -12,7 +12,8 @@ namespace rfim {
 
 // How one realization is mapped onto CTAs: a cluster of S CTAs (z slabs of L/S planes each)
 // holds G replicas; every thread updates a word of the slab for GT of them at once (so one field
-// load serves GT replicas).  Grid = ceil(R / G) clusters.
+// load serves GT replicas).  Grid = ceil(R / G) clusters.  S == 0 selects the grid-wide
+// cooperative kernel (kernels_grid.cuh): groups of 4 replicas, planes spread over one CTA per SM.
 struct BitsPlan {
   int32_t L = 0, S = 1, G = 1, GT = 1, threads = 256;
   size_t smem = 0;
@@ -22,6 +23,11 @@ struct BitsPlan {
   long long *partB = nullptr, *partM = nullptr, *partFi = nullptr;
   double *partF = nullptr;
   unsigned int *counter = nullptr;
+  // grid-wide plan (S == 0): per-(replica, slab) partials, per-CTA progress words, SM count
+  long long *gpartB = nullptr, *gpartM = nullptr, *gpartFi = nullptr;
+  double *gpartF = nullptr;
+  unsigned int *prog = nullptr;
+  int32_t sms = 0;
 };
 
 bool bits_supported(int32_t L);

@@ -50,3 +50,10 @@ def test_create_without_gpu_fails_loudly():
     import paper_1508_06268_gb300 as rf
     with pytest.raises(rf.RfimError):
         rf.Realization(8, [1.0, 2.0], stream=0)
+
+
+@pytest.mark.parametrize("L,R,P", [(64, 128, 152), (64, 128, 144), (64, 70, 152), (64, 8, 42), (32, 64, 152),
+                                   (64, 6, 10), (16, 4, 3)])
+def test_grid_partition(L, R, P):
+    import paper_1508_06268_gb300 as rf
+    assert rf.selftest_grid(L, R, P) == 0

@@ -344,3 +344,18 @@ def test_warp_specialised_variant_matches(kind, monkeypatch):
     np.testing.assert_array_equal(a["spins"], b["spins"])
     np.testing.assert_array_equal(a["t2r"], b["t2r"])
     np.testing.assert_array_equal(ref.observables()["sums"], ws.observables()["sums"])
+
+
+@pytest.mark.parametrize("L,R", [(64, 6), (64, 70), (32, 64)])
+def test_grid_wide_variant_bit_exact(L, R, monkeypatch):
+    """The cooperative grid-wide plan (shape 0,4,4,512: replica groups x z planes over one CTA
+    per SM, halos through L2) against the oracle, bimodal field, including partial groups."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    monkeypatch.setenv("RFIM_BITS_PLAN", "0,4,4,512")
+    g = rf.Realization(L, temps, h=1.5, field_kind=BIM, field_seed=3, seed=42, layout=BP)
+    monkeypatch.delenv("RFIM_BITS_PLAN")
+    o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=3, seed=42)
+    g.run(6, 3, 0)
+    o.run(6, 3, 0)
+    assert_same_state(g, o, "grid plan")
+    np.testing.assert_array_equal(g.observables()["sums"], o.observables())
