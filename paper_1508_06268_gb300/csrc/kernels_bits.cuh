@@ -25,6 +25,12 @@
 
 namespace rfim {
 
+#ifndef RFIM_BLOCK_UNROLL
+#define RFIM_BLOCK_UNROLL 8
+#endif
+// Unroll factor of the Philox-block loop of the sweep (compile-time experiment knob).
+constexpr int kBlockUnroll = RFIM_BLOCK_UNROLL;
+
 // Per-realization progress kept on the device by batched launches: the last work item of a
 // realization advances it after the exchange step (sweep and exchange counters, intervals left).
 struct SlotCtl {
@@ -348,7 +354,7 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
         for (int gg = 0; gg < GT; ++gg)
 #pragma unroll
           for (int k = 0; k < 4; ++k) fk[gg][k] = 0u;
-#pragma unroll
+#pragma unroll kBlockUnroll
         for (int jj = 0; jj < 8; ++jj) {
           const int j = 7 - jj;
 #pragma unroll

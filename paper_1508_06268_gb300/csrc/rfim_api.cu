@@ -317,10 +317,8 @@ int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
     if (k > 0 && !(cfg->temps[k] > cfg->temps[k - 1]))
       return fail(nullptr, RFIM_EINVAL, "temperatures must be strictly ascending");
   }
-  BitsPlan plan;
-  if (cfg->layout == RFIM_LAYOUT_BITPACK) {
-    if (!bits_supported(L)) return fail(nullptr, RFIM_EINVAL, "bit layout supports L in {8,16,32,64} (got %d)", L);
-  }
+  if (cfg->layout == RFIM_LAYOUT_BITPACK && !bits_supported(L))
+    return fail(nullptr, RFIM_EINVAL, "bit layout supports L in {8,16,32,64} (got %d)", L);
 
   rfim_ctx *c = new rfim_ctx();
   cudaGetDevice(&c->device);
