@@ -12,7 +12,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/rfim.h"
+#include "rfim.h"
 #include "bits_layout.cuh"
 #include "exchange.cuh"
 #include "internal.h"

@@ -93,7 +93,7 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
 size_t grid_smem(int L, int max_units) {
   const size_t PW = (size_t)L * L / 64;
   const size_t need = (size_t)max_units * kGridGroup * 2 * PW * 4 + (size_t)kGridMaxPieces * 2 * kGridGroup * PW * 4 +
-                      (size_t)kGridMaxPieces * kGridGroup * 128;
+                      tab_bytes(kGridMaxPieces * kGridGroup);
   return std::max(need, kGridMinSmem);
 }
 
@@ -203,7 +203,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   }
   if (!gfn)
     p.smem = p.threads == kWsThreads ? ws_smem(L, p.S, p.G)
-                                      : (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + (size_t)p.G * 128;
+                                      : (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + tab_bytes(p.G);
   if (p.smem > 227 * 1024) {
     if (err) *err = "bit-layout plan exceeds shared memory";
     return -1;

@@ -119,9 +119,77 @@ __device__ __forceinline__ uint32_t block_offsets(const PairSlices &p, int j) {
   if (BIM) {
     const uint32_t f = (j & 1) ? p.f3 : p.f4;   // field bit at 2m+4 (cyclic)
     z = mux(f, z, rotl(0x01010101u, (2 * m + 4) & 31));
-    return rotr(z, (2 * m - 2) & 31);           // bit 2m -> bit 2 of every byte
+    return rotr(z, (2 * m - 2) & 31) & 0x7C7C7C7Cu;  // bit 2m -> bit 2 of every byte
   }
-  return rotr(z, (2 * m - 3) & 31);             // bit 2m -> bit 3 of every byte
+  return rotr(z, (2 * m - 3) & 31) & 0x78787878u;    // bit 2m -> bit 3 of every byte
+}
+
+// ---- per-replica decision tables in shared memory ------------------------------------------
+// A replica's table (bimodal: 32 thresholds - 1, indexed by up-count, spin, field bit; float
+// field: 16 pairs (J n, b), b = fl(-2 beta log2 e) signed by the spin, indexed by up-count and
+// spin) sits in its own 256-byte slot aligned to 256 bytes.  Byte k of a block's
+// offset word then holds site k's byte offset within the slot, and one byte permute with the
+// slot address forms the entry address.
+constexpr uint32_t kTabSlot = 256;
+
+// Dynamic shared-memory bytes for n tables, with the alignment slack.
+__host__ __device__ constexpr size_t tab_bytes(int n) { return (size_t)(n + 1) * kTabSlot; }
+
+// Shared-window address of the first slot at or after p.
+__device__ __forceinline__ uint32_t tab_slot0(const void *p) {
+  return ((uint32_t)__cvta_generic_to_shared(p) + kTabSlot - 1u) & ~(kTabSlot - 1u);
+}
+
+// Fills the tables of n replicas, slot g for replica replica_of(g), with all threads of the CTA.
+// `base` is any generic pointer into dynamic shared memory at or before the slots.
+template <bool BIM, class F>
+__device__ __forceinline__ void tab_fill(const RealView &v, void *base, uint32_t slot0, int n, F replica_of) {
+  constexpr int E = BIM ? 32 : 16;
+  char *gen = reinterpret_cast<char *>(base) + (slot0 - (uint32_t)__cvta_generic_to_shared(base));
+  for (int t = threadIdx.x; t < n * E; t += blockDim.x) {
+    const int g = t / E, i = t % E;
+    const int k = v.r2t[replica_of(g)];
+    char *slot = gen + (size_t)g * kTabSlot;
+    if (BIM) {
+      reinterpret_cast<uint32_t *>(slot)[i] = v.thr[(int64_t)k * 32 + i];
+    } else {
+      const float b = (i >> 3) ? v.b2l[k] : -v.b2l[k];
+      reinterpret_cast<float2 *>(slot)[i] = make_float2(v.gjn[i & 7], b);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t r;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(a));
+  return r;
+}
+
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 r;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(a));
+  return r;
+}
+
+// Decisions of Philox block j of one word of one replica: sites 4j + k (k = 0..3) at bits 8k + j,
+// table slot `slot`, float field h4 of those sites.  Bimodal: accepted sites set their bit of
+// `flip`; float field: the acceptance sign bits are shifted into fk[k] (blocks visited j = 7..0,
+// so block j ends at bit j of fk[k]).
+template <bool BIM>
+__device__ __forceinline__ void decide_block(const Words4 &w, const PairSlices &ps, int j, uint32_t slot,
+                                             const float4 &h4, uint32_t &flip, uint32_t (&fk)[4]) {
+  const uint32_t offs = block_offsets<BIM>(ps, j);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t a = __byte_perm(offs, slot, 0x7650u | (uint32_t)k);
+    if (BIM) {
+      if (accept_table(w.w[k], lds_u32(a))) flip |= 1u << (8 * k + j);
+    } else {
+      const float hk = k == 0 ? h4.x : k == 1 ? h4.y : k == 2 ? h4.z : h4.w;
+      const float2 e = lds_f2(a);
+      fk[k] = __funnelshift_l(accept_float_sign(w.w[k], e.x, hk, e.y), fk[k], 1);
+    }
+  }
 }
 
 // The six other-colour neighbour words of local word (zl, iw) from plane array O (this CTA's
@@ -291,26 +359,15 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
   const int z0 = rank * PZ;
   __syncthreads();  // a CTA may run several intervals back to back: shared memory is reused
   uint32_t *sp = sm;                        // [G][2][WC]
-  uint32_t *tab = sm + (size_t)G * 2 * WC;  // BIM: [G][32] uint32; else [G][16] float2
+  uint32_t *tab = sm + (size_t)G * 2 * WC;  // G decision-table slots
+  const uint32_t slot0 = tab_slot0(tab);
   const int nt = blockDim.x, tid = threadIdx.x;
 
   for (int t = tid; t < gact * 2 * WC; t += nt) {
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     sp[t] = v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl];
   }
-  if (BIM) {
-    for (int t = tid; t < gact * 32; t += nt) {
-      const int g = t >> 5;
-      tab[t] = v.thr[(int64_t)v.r2t[r0 + g] * 32 + (t & 31)];
-    }
-  } else {
-    float2 *gt = reinterpret_cast<float2 *>(tab);
-    for (int t = tid; t < gact * 16; t += nt) {
-      const int g = t >> 4, i = t & 15;
-      const float b = v.b2l[v.r2t[r0 + g]];
-      gt[t] = make_float2(v.gjn[i & 7], (i >> 3) ? b : -b);
-    }
-  }
+  tab_fill<BIM>(v, tab, slot0, gact, [&](int g) { return r0 + g; });
   sync_slabs<S>();
 
   const int ngroups = (gact + GT - 1) / GT;
@@ -326,7 +383,7 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
         const int zl = wl / P, iw = wl % P;
         const int z = z0 + zl;
         const int64_t wq = (int64_t)z * P + iw;
-        float4 hh4[8];
+        float4 hh4[8] = {};
         if (!BIM) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
@@ -347,8 +404,7 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
 #pragma unroll
         for (int gg = 0; gg < GT; ++gg) ps[gg] = make_pairs(c0[gg], c1[gg], c2[gg], sf[gg], fb);
         // replicas past the end of a partial group repeat the last one; only their write is skipped.
-        // Float field: the acceptance of site (j, k) is the sign bit of rz(word) - 2^t 2^32, shifted
-        // into fk[k] (blocks visited j = 7..0, so block j ends at bit j); flip = fk[k] << 8k.
+        // Float field: flip = fk[k] << 8k once all blocks are done.
         uint32_t fk[GT][4];
 #pragma unroll
         for (int gg = 0; gg < GT; ++gg)
@@ -361,19 +417,7 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
           for (int gg = 0; gg < GT; ++gg) {
             const int g = min(grp * GT + gg, gact - 1);
             const Words4 w = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), sweep, tag);
-            const uint32_t acc = block_offsets<BIM>(ps[gg], j);
-            const char *tb = reinterpret_cast<const char *>(tab) + g * 128;
-            const float hk[4] = {hh4[j].x, hh4[j].y, hh4[j].z, hh4[j].w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint32_t off = (acc >> (8 * k)) & (BIM ? 0x7Cu : 0x78u);
-              if (BIM) {
-                if (accept_table(w.w[k], *reinterpret_cast<const uint32_t *>(tb + off))) flip[gg] |= 1u << (8 * k + j);
-              } else {
-                const float2 e = *reinterpret_cast<const float2 *>(tb + off);
-                fk[gg][k] = __funnelshift_l(accept_float_sign(w.w[k], e.x, hk[k], e.y), fk[gg][k], 1);
-              }
-            }
+            decide_block<BIM>(w, ps[gg], j, slot0 + (uint32_t)g * kTabSlot, hh4[j], flip[gg], fk[gg]);
           }
         }
         if (!BIM) {

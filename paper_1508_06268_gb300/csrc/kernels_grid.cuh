@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
   const int np = np_s, nu = nu_s, nb = nb_s;
   uint32_t *lat = sm;                                          // [max_units][GG][2][PW]
   uint32_t *halo = lat + (size_t)ga.max_units * GG * 2 * PW;  // [pieces][2][GG][PW] (other colour)
-  uint32_t *tab = halo + (size_t)kGridMaxPieces * 2 * GG * PW;  // [pieces][GG] x 128 bytes
+  uint32_t *tab = halo + (size_t)kGridMaxPieces * 2 * GG * PW;  // [pieces][GG] decision-table slots
+  const uint32_t slot0 = tab_slot0(tab);
   auto lat_at = [&](int lu, int gg, int c) { return lat + ((size_t)(lu * GG + gg) * 2 + c) * PW; };
   auto halo_at = [&](int p, int side, int gg) { return halo + ((size_t)(p * 2 + side) * GG + gg) * PW; };
   auto gact_of = [&](int p) { return min(GG, v.R - pc[p].g * GG); };
@@ -98,16 +99,7 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
     const int r = q.g * GG + gg, z = q.z0 + (lu - q.lu0);
     lat[t] = r < v.R ? v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] : 0u;
   }
-  for (int t = tid; t < np * GG * 32; t += nt) {
-    const int p = t / (GG * 32), gg = (t / 32) % GG, i = t % 32;
-    const int r = min(pc[p].g * GG + gg, v.R - 1);
-    if (BIM) {
-      tab[t] = v.thr[(int64_t)v.r2t[r] * 32 + i];
-    } else if (i < 16) {
-      const float b = v.b2l[v.r2t[r]];
-      reinterpret_cast<float2 *>(tab)[(p * GG + gg) * 16 + i] = make_float2(v.gjn[i & 7], (i >> 3) ? b : -b);
-    }
-  }
+  tab_fill<BIM>(v, tab, slot0, np * GG, [&](int t) { return min(pc[t / GG].g * GG + t % GG, v.R - 1); });
   __syncthreads();
 
   const int items = nu * PW;
@@ -156,7 +148,7 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
         const int z = pc[p].z0 + (lu - pc[p].lu0);
         const int64_t wq = (int64_t)z * PW + w;
         const int gact = gact_of(p);
-        float4 hh4[8];
+        float4 hh4[8] = {};
         if (!BIM) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
@@ -187,19 +179,7 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
             const int g = min(gg, gact - 1);
             const int r = pc[p].g * GG + g;
             const Words4 wd = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)r, sweep, tag);
-            const uint32_t acc = block_offsets<BIM>(ps[gg], j);
-            const char *tb = reinterpret_cast<const char *>(tab) + (p * GG + g) * 128;
-            const float hk[4] = {hh4[j].x, hh4[j].y, hh4[j].z, hh4[j].w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t off = (acc >> (8 * q)) & (BIM ? 0x7Cu : 0x78u);
-              if (BIM) {
-                if (accept_table(wd.w[q], *reinterpret_cast<const uint32_t *>(tb + off))) flip[gg] |= 1u << (8 * q + j);
-              } else {
-                const float2 e = *reinterpret_cast<const float2 *>(tb + off);
-                fk[gg][q] = __funnelshift_l(accept_float_sign(wd.w[q], e.x, hk[q], e.y), fk[gg][q], 1);
-              }
-            }
+            decide_block<BIM>(wd, ps[gg], j, slot0 + (uint32_t)(p * GG + g) * kTabSlot, hh4[j], flip[gg], fk[gg]);
           }
         }
 #pragma unroll

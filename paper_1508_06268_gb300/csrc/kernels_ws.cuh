@@ -70,8 +70,8 @@ __device__ __forceinline__ void ws_interval(const RealView &v, int G, int r0, in
   const int up_rank = (rank + 1) % S, dn_rank = (rank + S - 1) % S;
   const int z0 = rank * PZ;
   uint32_t *sp = sm;                                        // [G][2][WC]
-  uint32_t *tab = sm + (size_t)G * 2 * WC;                  // [G] x 128 bytes
-  uint4 *ring = reinterpret_cast<uint4 *>(tab + (size_t)G * 32);  // [16][NS][GT*32] uint4
+  uint32_t *tab = sm + (size_t)G * 2 * WC;                  // G decision-table slots
+  uint4 *ring = reinterpret_cast<uint4 *>(tab + tab_bytes(G) / 4);  // [16][NS][GT*32] uint4
   uint64_t *bars = reinterpret_cast<uint64_t *>(ring + (size_t)kWsConsumerWarps * kWsStages * GT * 32);
   // bars: full[16][NS], empty[16][NS]
   const int nt = blockDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -80,16 +80,8 @@ __device__ __forceinline__ void ws_interval(const RealView &v, int G, int r0, in
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     sp[t] = v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl];
   }
-  if (BIM) {
-    for (int t = tid; t < gact * 32; t += nt) tab[t] = v.thr[(int64_t)v.r2t[r0 + (t >> 5)] * 32 + (t & 31)];
-  } else {
-    float2 *gt = reinterpret_cast<float2 *>(tab);
-    for (int t = tid; t < gact * 16; t += nt) {
-      const int g = t >> 4, i = t & 15;
-      const float b = v.b2l[v.r2t[r0 + g]];
-      gt[t] = make_float2(v.gjn[i & 7], (i >> 3) ? b : -b);
-    }
-  }
+  const uint32_t slot0 = tab_slot0(tab);
+  tab_fill<BIM>(v, tab, slot0, gact, [&](int g) { return r0 + g; });
   __shared__ int ws_abort;
   if (tid == 0) ws_abort = 0;
   if (tid < 2 * kWsConsumerWarps * kWsStages) mbar_init(bars + tid, 1);
@@ -178,20 +170,8 @@ __device__ __forceinline__ void ws_interval(const RealView &v, int G, int r0, in
 #pragma unroll
             for (int gg = 0; gg < GT; ++gg) {
               const int g = min(gg, gact - 1);
-              const uint32_t ww[4] = {wr[gg].x, wr[gg].y, wr[gg].z, wr[gg].w};
-              const uint32_t acc = block_offsets<BIM>(ps[gg], j);
-              const char *tb = reinterpret_cast<const char *>(tab) + g * 128;
-              const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const uint32_t off = (acc >> (8 * k)) & (BIM ? 0x7Cu : 0x78u);
-                if (BIM) {
-                  if (accept_table(ww[k], *reinterpret_cast<const uint32_t *>(tb + off))) flip[gg] |= 1u << (8 * k + j);
-                } else {
-                  const float2 e = *reinterpret_cast<const float2 *>(tb + off);
-                  fk[gg][k] = __funnelshift_l(accept_float_sign(ww[k], e.x, hk[k], e.y), fk[gg][k], 1);
-                }
-              }
+              const Words4 ww = {{wr[gg].x, wr[gg].y, wr[gg].z, wr[gg].w}};
+              decide_block<BIM>(ww, ps[gg], j, slot0 + (uint32_t)g * kTabSlot, q4, flip[gg], fk[gg]);
             }
           }
           if (live) {
@@ -228,7 +208,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_sweeps_ws(RealView v, int32_t
 
 // Dynamic shared memory of the warp-specialised kernel for L / S and G replicas.
 __host__ __device__ constexpr size_t ws_smem(int L, int S, int G) {
-  return (size_t)G * 2 * ((size_t)(L / S) * (L * L / 64)) * 4 + (size_t)G * 128 +
+  return (size_t)G * 2 * ((size_t)(L / S) * (L * L / 64)) * 4 + tab_bytes(G) +
          (size_t)kWsConsumerWarps * kWsStages * kWsStageBytes + (size_t)2 * kWsConsumerWarps * kWsStages * 8;
 }
 

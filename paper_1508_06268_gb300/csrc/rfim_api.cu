@@ -11,7 +11,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/rfim.h"
+#include "rfim.h"
 #include "internal.h"
 #include "sweep_bits.h"
 

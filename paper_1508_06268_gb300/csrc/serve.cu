@@ -16,7 +16,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/rfim.h"
+#include "rfim.h"
 #include "batch.h"
 #include "internal.h"
 #include "sweep_bits.h"
