@@ -59,9 +59,17 @@ int words_per_cta(int L, int S) { return L <= 0 || S <= 0 ? 0 : (L / S) * (L * L
 
 using GridFn = void (*)(RealView, GridArgs, uint32_t, int32_t, const float4 *, ExchArgs);
 
-GridFn grid_kernel_for(int L, bool bim) {
-  if (L == 64) return bim ? (GridFn)k_sweeps_grid<64, true> : (GridFn)k_sweeps_grid<64, false>;
-  if (L == 32) return bim ? (GridFn)k_sweeps_grid<32, true> : (GridFn)k_sweeps_grid<32, false>;
+template <int L, int GTI>
+GridFn grid_pick(bool bim) {
+  return bim ? (GridFn)k_sweeps_grid<L, true, GTI> : (GridFn)k_sweeps_grid<L, false, GTI>;
+}
+
+// Grid-wide instances: replicas per thread item GT = 4 (one field load per group) or 1.
+GridFn grid_kernel_for(int L, int GT, bool bim) {
+  if (L == 64 && GT == 4) return grid_pick<64, 4>(bim);
+  if (L == 64 && GT == 1) return grid_pick<64, 1>(bim);
+  if (L == 32 && GT == 4) return grid_pick<32, 4>(bim);
+  if (L == 32 && GT == 1) return grid_pick<32, 1>(bim);
   return nullptr;
 }
 
@@ -127,8 +135,8 @@ void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &
 
 std::vector<std::string> plan_candidates(int32_t L) {
   if (L == 64)
-    return {"4,4,4,512", "0,4,4,512", "0,4,4,448", "4,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
-  if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512"};
+    return {"4,4,4,512", "0,4,4,512", "0,4,1,512", "4,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
+  if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512", "0,4,1,512"};
   if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
   return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
 }
@@ -169,19 +177,21 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
     // ignored and the defaults stand
     const bool named = sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4;
-    const bool exists = named && (s == 0 ? (gt == kGridGroup && th >= 256 && th <= 512 && grid_kernel_for(L, bimodal))
+    const bool exists = named && (s == 0 ? (th >= 256 && th <= 512 && th % 32 == 0 && grid_kernel_for(L, gt, bimodal))
                                          : kernel_for(L, s, gt, th, bimodal) != nullptr);
     if (exists) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;
     }
   }
-  if (p.G > Rcap) p.G = Rcap;
-  if (p.GT > p.G) p.GT = 1;
-  if (p.G % p.GT) p.G = (p.G / p.GT) * p.GT;
+  if (p.S != 0) {
+    if (p.G > Rcap) p.G = Rcap;
+    if (p.GT > p.G) p.GT = 1;
+    if (p.G % p.GT) p.G = (p.G / p.GT) * p.GT;
+  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal);
-  GridFn gfn = p.S == 0 && p.GT == kGridGroup && p.threads >= 256 && p.threads <= 512 ? grid_kernel_for(L, bimodal) : nullptr;
+  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 512 ? grid_kernel_for(L, p.GT, bimodal) : nullptr;
   if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
@@ -295,7 +305,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.ctl = nullptr;
   xa.err = plan.counter + 1;
   if (plan.S == 0) {
-    GridFn gfn = grid_kernel_for(plan.L, v.kind == kBimodal);
+    GridFn gfn = grid_kernel_for(plan.L, plan.GT, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;
     GridArgs ga = grid_args(plan, v.R, plan.sms);
     cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);

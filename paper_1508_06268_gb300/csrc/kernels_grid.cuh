@@ -1,5 +1,8 @@
 // Grid-wide bit-layout sweep: one cooperative launch with one CTA per SM covers every SM, whatever
-// the replica count.  Same arithmetic and decisions as kernels_bits.cuh.
+// the replica count.  Same arithmetic and decisions as kernels_bits.cuh.  A thread item is one
+// 32-site word of GTI replicas of a group (GTI = 4: the field of the word is loaded once for the
+// group; GTI = 1: four times more, smaller items, so that the items of a CTA split into nearly
+// whole rounds of its threads).
 //
 // The realization's (4-replica group, z plane) units are split evenly over the CTAs
 // (grid_partition.cuh); each CTA keeps its planes of both colours in shared memory for the whole
@@ -50,7 +53,7 @@ __device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned 
   return false;
 }
 
-template <int L, bool BIM>
+template <int L, bool BIM, int GTI>
 __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
                                                         const float4 *__restrict__ field4, ExchArgs xa) {
   constexpr int PW = L * L / 64, W = L * L * L / 64;
@@ -102,8 +105,9 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
   tab_fill<BIM>(v, tab, slot0, np * GG, [&](int t) { return min(pc[t / GG].g * GG + t % GG, v.R - 1); });
   __syncthreads();
 
-  const int items = nu * PW;
-  const int phase_a = ((nu - nb) * PW / nt) * nt;  // whole rounds of interior planes
+  constexpr int IPW = PW * (GG / GTI);  // items per plane
+  const int items = nu * IPW;
+  const int phase_a = ((nu - nb) * IPW / nt) * nt;  // whole rounds of interior planes
   unsigned *err = xa.err;
 
   // Loads the other colour's end planes of every piece's z neighbours once they have finished
@@ -143,23 +147,25 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
     auto process = [&](int i0, int i1) {
 #pragma unroll 1
       for (int it = i0 + tid; it < i1; it += nt) {
-        const int lu = order[it / PW], w = it % PW;
+        const int lu = order[it / IPW], w = it % PW;
+        const int gb = (it % IPW) / PW * GTI;  // first replica of this item within the group
         const int p = plane_piece[lu];
         const int z = pc[p].z0 + (lu - pc[p].lu0);
         const int64_t wq = (int64_t)z * PW + w;
         const int gact = gact_of(p);
+        if (gb >= gact) continue;  // GTI = 1: replica past the end of a partial group
         float4 hh4[8] = {};
         if (!BIM) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
         }
         const uint32_t p0 = parity0_mask<L>(c, z, w);
-        PairSlices ps[GG];
-        uint32_t sf[GG], flip[GG], fk[GG][4];
+        PairSlices ps[GTI];
+        uint32_t sf[GTI], flip[GTI], fk[GTI][4];
         const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
 #pragma unroll
-        for (int gg = 0; gg < GG; ++gg) {
-          const int g = min(gg, gact - 1);
+        for (int gg = 0; gg < GTI; ++gg) {
+          const int g = min(gb + gg, gact - 1);
           const uint32_t *O = lat_at(lu, g, other);
           uint32_t nbw[6], c0, c1, c2;
           nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], p0, nbw[0], nbw[1], nbw[2], nbw[3]);
@@ -175,18 +181,18 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
         for (int jj = 0; jj < 8; ++jj) {
           const int j = 7 - jj;
 #pragma unroll
-          for (int gg = 0; gg < GG; ++gg) {
-            const int g = min(gg, gact - 1);
+          for (int gg = 0; gg < GTI; ++gg) {
+            const int g = min(gb + gg, gact - 1);
             const int r = pc[p].g * GG + g;
             const Words4 wd = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)r, sweep, tag);
             decide_block<BIM>(wd, ps[gg], j, slot0 + (uint32_t)(p * GG + g) * kTabSlot, hh4[j], flip[gg], fk[gg]);
           }
         }
 #pragma unroll
-        for (int gg = 0; gg < GG; ++gg) {
-          if (gg >= gact) continue;
+        for (int gg = 0; gg < GTI; ++gg) {
+          if (gb + gg >= gact) continue;
           if (!BIM) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
-          lat_at(lu, gg, c)[w] = sf[gg] ^ flip[gg];
+          lat_at(lu, gb + gg, c)[w] = sf[gg] ^ flip[gg];
         }
       }
     };
@@ -202,9 +208,13 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
       const int r = pc[p].g * GG + gg, z = pc[p].z0 + (lu - pc[p].lu0);
       v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = lat_at(lu, gg, c)[w];
     }
-    __threadfence();
+    // the CTA barrier orders every thread's end-plane stores before thread 0's gpu-scope fence
+    // and release (cumulativity), as in a grid-wide barrier
     __syncthreads();
-    if (tid == 0) st_release_u32(ga.prog + k, (unsigned)(h + 1));
+    if (tid == 0) {
+      __threadfence();
+      st_release_u32(ga.prog + k, (unsigned)(h + 1));
+    }
   }
 
   for (int t = tid; t < nu * GG * 2 * PW; t += nt) {

@@ -346,12 +346,14 @@ def test_warp_specialised_variant_matches(kind, monkeypatch):
     np.testing.assert_array_equal(ref.observables()["sums"], ws.observables()["sums"])
 
 
-@pytest.mark.parametrize("L,R", [(64, 6), (64, 70), (32, 64)])
-def test_grid_wide_variant_bit_exact(L, R, monkeypatch):
-    """The cooperative grid-wide plan (shape 0,4,4,512: replica groups x z planes over one CTA
-    per SM, halos through L2) against the oracle, bimodal field, including partial groups."""
+@pytest.mark.parametrize("L,R,plan", [(64, 6, "0,4,4,512"), (64, 70, "0,4,4,512"), (32, 64, "0,4,4,512"),
+                                       (64, 6, "0,4,1,512"), (64, 70, "0,4,1,512"), (32, 64, "0,4,1,384")])
+def test_grid_wide_variant_bit_exact(L, R, plan, monkeypatch):
+    """The cooperative grid-wide plans (shape 0,4,GT,threads: replica groups x z planes over one
+    CTA per SM, halos through L2, GT replicas per thread item) against the oracle, bimodal field,
+    including partial groups."""
     temps = inputs.geometric_temps(1.0, 5.0, R)
-    monkeypatch.setenv("RFIM_BITS_PLAN", "0,4,4,512")
+    monkeypatch.setenv("RFIM_BITS_PLAN", plan)
     g = rf.Realization(L, temps, h=1.5, field_kind=BIM, field_seed=3, seed=42, layout=BP)
     monkeypatch.delenv("RFIM_BITS_PLAN")
     o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=3, seed=42)
@@ -359,3 +361,23 @@ def test_grid_wide_variant_bit_exact(L, R, monkeypatch):
     o.run(6, 3, 0)
     assert_same_state(g, o, "grid plan")
     np.testing.assert_array_equal(g.observables()["sums"], o.observables())
+
+
+@pytest.mark.parametrize("plan", ["0,4,4,512", "0,4,1,512"])
+def test_grid_wide_variant_gaussian_matches_cluster_plan(plan, monkeypatch):
+    """Gaussian field: the grid-wide plans take the same decisions as the default cluster plan
+    (spins and permutation identical; energies summed over other slab boundaries agree to
+    rounding)."""
+    L, R = 64, 10
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 77)
+    ref = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP, seed=5)
+    monkeypatch.setenv("RFIM_BITS_PLAN", plan)
+    grid = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP, seed=5)
+    monkeypatch.delenv("RFIM_BITS_PLAN")
+    for g in (ref, grid):
+        g.run(12, 3, 0)
+    a, b = ref.get_state(), grid.get_state()
+    np.testing.assert_array_equal(a["spins"], b["spins"])
+    np.testing.assert_array_equal(a["t2r"], b["t2r"])
+    np.testing.assert_allclose(ref.observables()["sums"], grid.observables()["sums"], rtol=1e-12)
