@@ -348,7 +348,7 @@ def main():
                 "frac": achieved / peak,
                 "traffic": SWEEP_TRAFFIC_BYTES.get("k_sweeps_bits") if layout == rf.LAYOUT_BITPACK else None,
                 "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
-                "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8",
+                "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8_rows",
                 "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
                               f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
                               f"{sm_mhz:.0f} MHz (median sampled)",

@@ -180,6 +180,86 @@ __global__ void k_energy(RealView v, double J, double h, bool bitpack) {
   }
 }
 
+// The same energies for the int8 layout when L % 8 == 0, four sites per step: each neighbour
+// direction of a group of four same-colour sites is one 32-bit word of 0/1 bytes (see the int8
+// sweep), so s_i s_j summed over the group is 4 - 2 popc(self ^ neighbour word).
+__global__ void k_energy_int8_rows(RealView v, double J, double h) {
+  const int32_t r = blockIdx.x;
+  const int32_t L = v.L, Lh = v.Lh;
+  const int64_t half = (int64_t)v.N / 2, plane = (int64_t)L * Lh, groups = half / 4;
+  const uint8_t *S0 = v.spins8 + (int64_t)r * 2 * half, *S1 = S0 + half;
+  auto ld = [](const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); };
+  long long B = 0, M = 0, Fi = 0;
+  float fs = 0.0f, fe = 0.0f;
+  for (int32_t c = 0; c < 2; ++c) {
+    const uint8_t *S = c ? S1 : S0;
+    for (int64_t g = threadIdx.x; g < groups; g += blockDim.x) {
+      const int64_t q0 = 4 * g;
+      const uint32_t self = ld(S + q0);
+      M += 2 * __popc(self) - 4;
+      if (c == 0) {
+        const int32_t xh0 = (int32_t)(q0 % Lh);
+        const int64_t row = q0 / Lh;
+        const int32_t y = (int32_t)(row % L), z = (int32_t)(row / L);
+        const uint32_t par = (uint32_t)((y + z) & 1);
+        const uint32_t w0 = ld(S1 + q0);
+        const int32_t xa = par ? (xh0 + 4 == Lh ? 0 : xh0 + 4) : (xh0 == 0 ? Lh - 4 : xh0 - 4);
+        const uint32_t wa = ld(S1 + (q0 - xh0) + xa);
+        const uint32_t wx = par ? __byte_perm(w0, wa, 0x4321u) : __byte_perm(wa, w0, 0x6543u);
+        const uint32_t wyp = ld(S1 + (y == L - 1 ? q0 + Lh - plane : q0 + Lh));
+        const uint32_t wym = ld(S1 + (y == 0 ? q0 - Lh + plane : q0 - Lh));
+        const uint32_t wzp = ld(S1 + (z == L - 1 ? q0 + plane - half : q0 + plane));
+        const uint32_t wzm = ld(S1 + (z == 0 ? q0 - plane + half : q0 - plane));
+        B += 24 - 2 * (__popc(self ^ w0) + __popc(self ^ wx) + __popc(self ^ wyp) + __popc(self ^ wym) +
+                       __popc(self ^ wzp) + __popc(self ^ wzm));
+      }
+      if (v.kind == kBimodal) {
+        Fi += 4 - 2 * __popc(self ^ ld(v.hbit_c + c * half + q0));
+      } else {
+        const float4 h4 = *reinterpret_cast<const float4 *>(v.hh_c + c * half + q0);
+        const float hk[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float term = ((self >> (8 * j)) & 1u) ? hk[j] : -hk[j];
+          const float t = __fadd_rn(fs, term);
+          const float bp = __fsub_rn(t, fs);
+          const float err = __fadd_rn(__fsub_rn(fs, __fsub_rn(t, bp)), __fsub_rn(term, bp));
+          fs = t;
+          fe = __fadd_rn(fe, err);
+        }
+      }
+    }
+  }
+  double F = (double)fs + (double)fe;
+  __shared__ long long sB[32], sM[32], sF[32];
+  __shared__ double sD[32];
+  B = warp_sum(B);
+  M = warp_sum(M);
+  Fi = warp_sum(Fi);
+  F = warp_sum(F);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    sB[wid] = B;
+    sM[wid] = M;
+    sF[wid] = Fi;
+    sD[wid] = F;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tb = 0, tm = 0, tf = 0;
+    double td = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      tb += sB[w];
+      tm += sM[w];
+      tf += sF[w];
+      td += sD[w];
+    }
+    const double Fv = v.kind == kBimodal ? h * (double)tf : td;
+    v.E[r] = -J * (double)tb - Fv;
+    v.M[r] = tm;
+  }
+}
+
 // One exchange step j plus measurement (exchange.cuh), one CTA.
 __global__ void k_exchange(RealView v, uint32_t j, int64_t measure_from) { exchange_and_measure(v, j, measure_from); }
 
@@ -242,7 +322,10 @@ cudaError_t launch_init_spins(const RealView &v, int32_t R, uint32_t stage, bool
 }
 
 cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st) {
-  k_energy<<<v.R, 512, 0, st>>>(v, J, h, bitpack);
+  if (!bitpack && v.L % 8 == 0)
+    k_energy_int8_rows<<<v.R, 512, 0, st>>>(v, J, h);
+  else
+    k_energy<<<v.R, 512, 0, st>>>(v, J, h, bitpack);
   return cudaGetLastError();
 }
 
