@@ -38,7 +38,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweeps_bits<64,4,4,float,512> launch (one
 # exchange interval, 3.36e8 attempts) from an ncu capture of this kernel version; None when the
 # kernel changed since (profiles/k_sweeps_bits_L64_R128_gaussian.md).
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.327872e6}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.32736e6, "k_halfsweep_int8_rows": None}
 
 
 def parse():
@@ -266,12 +266,16 @@ def run_serve(args):
 
 
 def run_int_rates():
-    """Builds and runs the GB300 issue-rate microbenchmark (the roofline's peak basis)."""
-    src = os.path.join(ROOT, "paper_1508_06268_gb300", "microbench", "int_rates.cu")
-    exe = os.path.join(ROOT, "paper_1508_06268_gb300", "_lib", "int_rates")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
-    subprocess.run([exe], check=True)
+    """Builds and runs the GB300 issue-rate microbenchmark (the roofline's peak basis) and the
+    instruction-mix ceiling of Philox plus the acceptance tests."""
+    mb = os.path.join(ROOT, "paper_1508_06268_gb300", "microbench")
+    csrc = os.path.join(ROOT, "paper_1508_06268_gb300", "csrc")
+    for name in ("int_rates", "mix_rates"):
+        exe = os.path.join(ROOT, "paper_1508_06268_gb300", "_lib", name)
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-I", csrc,
+                        "-o", exe, os.path.join(mb, name + ".cu")], check=True)
+        subprocess.run([exe], check=True)
 
 
 def main():

@@ -182,25 +182,27 @@ __global__ void k_energy(RealView v, double J, double h, bool bitpack) {
 
 // The same energies for the int8 layout when L % 8 == 0, four sites per step: each neighbour
 // direction of a group of four same-colour sites is one 32-bit word of 0/1 bytes (see the int8
-// sweep), so s_i s_j summed over the group is 4 - 2 popc(self ^ neighbour word).
+// sweep), so s_i s_j summed over the group is 4 - 2 popc(self ^ neighbour word).  LC: the edge
+// length when fixed at compile time, else 0.
+template <int LC>
 __global__ void k_energy_int8_rows(RealView v, double J, double h) {
   const int32_t r = blockIdx.x;
-  const int32_t L = v.L, Lh = v.Lh;
-  const int64_t half = (int64_t)v.N / 2, plane = (int64_t)L * Lh, groups = half / 4;
+  const int32_t L = LC ? LC : v.L, Lh = L / 2;
+  const int32_t half = L * L * Lh, plane = L * Lh, groups = half / 4;
   const uint8_t *S0 = v.spins8 + (int64_t)r * 2 * half, *S1 = S0 + half;
   auto ld = [](const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); };
   long long B = 0, M = 0, Fi = 0;
   float fs = 0.0f, fe = 0.0f;
   for (int32_t c = 0; c < 2; ++c) {
     const uint8_t *S = c ? S1 : S0;
-    for (int64_t g = threadIdx.x; g < groups; g += blockDim.x) {
-      const int64_t q0 = 4 * g;
+    for (int32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+      const int32_t q0 = 4 * g;
       const uint32_t self = ld(S + q0);
       M += 2 * __popc(self) - 4;
       if (c == 0) {
-        const int32_t xh0 = (int32_t)(q0 % Lh);
-        const int64_t row = q0 / Lh;
-        const int32_t y = (int32_t)(row % L), z = (int32_t)(row / L);
+        const int32_t xh0 = q0 % Lh;
+        const int32_t row = q0 / Lh;
+        const int32_t y = row % L, z = row / L;
         const uint32_t par = (uint32_t)((y + z) & 1);
         const uint32_t w0 = ld(S1 + q0);
         const int32_t xa = par ? (xh0 + 4 == Lh ? 0 : xh0 + 4) : (xh0 == 0 ? Lh - 4 : xh0 - 4);
@@ -322,9 +324,14 @@ cudaError_t launch_init_spins(const RealView &v, int32_t R, uint32_t stage, bool
 }
 
 cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st) {
-  if (!bitpack && v.L % 8 == 0)
-    k_energy_int8_rows<<<v.R, 512, 0, st>>>(v, J, h);
-  else
+  if (!bitpack && v.L % 8 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
+    switch (v.L) {
+      case 16: k_energy_int8_rows<16><<<v.R, 512, 0, st>>>(v, J, h); break;
+      case 32: k_energy_int8_rows<32><<<v.R, 512, 0, st>>>(v, J, h); break;
+      case 64: k_energy_int8_rows<64><<<v.R, 512, 0, st>>>(v, J, h); break;
+      default: k_energy_int8_rows<0><<<v.R, 512, 0, st>>>(v, J, h); break;
+    }
+  } else
     k_energy<<<v.R, 512, 0, st>>>(v, J, h, bitpack);
   return cudaGetLastError();
 }

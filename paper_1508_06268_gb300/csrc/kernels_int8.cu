@@ -71,13 +71,15 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 }
 
 // grid: x over the groups of four sites, y over groups of GT replicas (GT temperature tables per
-// CTA); a thread takes one group of four sites in GT replicas, which share the field load
-template <bool kBimodalField, int GT>
+// CTA); a thread takes one group of four sites in GT replicas, which share the field load.
+// LC: the edge length when fixed at compile time (index arithmetic by shifts, replica strides as
+// address offsets), 0 for any L divisible by 8.
+template <bool kBimodalField, int GT, int LC>
 __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int colour, uint32_t sweep) {
   __shared__ __align__(256) uint32_t tab[64 * GT];  // per replica a 256-byte slot: bimodal 32 x (thr - 1),
                                                     // float field 16 x (J n, +-b)
-  const int32_t L = v.L, Lh = v.Lh;
-  const int64_t half = (int64_t)v.N / 2, plane = (int64_t)L * Lh;
+  const int32_t L = LC ? LC : v.L, Lh = L / 2;
+  const int64_t half = (int64_t)L * L * Lh, plane = (int64_t)L * Lh;
   const int r0 = (int)blockIdx.y * GT;
   for (int t = threadIdx.x; t < GT * 32; t += blockDim.x) {
     const int gg = t >> 5, i = t & 31, r = min(r0 + gg, v.R - 1), k = v.r2t[r];
@@ -89,21 +91,21 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
     }
   }
   __syncthreads();
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t g = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (g >= half / 4) return;
   const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(tab);
-  const int64_t q0 = 4 * g;
-  const int32_t xh0 = (int32_t)(q0 % Lh);
-  const int64_t row = q0 / Lh;
-  const int32_t y = (int32_t)(row % L), z = (int32_t)(row / L);
+  const int32_t q0 = 4 * g;
+  const int32_t xh0 = q0 % Lh;
+  const int32_t row = q0 / Lh;
+  const int32_t y = row % L, z = row / L;
   const bool odd = ((colour + y + z) & 1) != 0;
   // x neighbours: the same word, and the word before (even rows: site x - 1) or after (odd rows:
   // x + 1), periodic within the row, shifted by one byte; y, z: periodic rows and planes
-  const int64_t qa = (q0 - xh0) + (odd ? (xh0 + 4 == Lh ? 0 : xh0 + 4) : (xh0 == 0 ? Lh - 4 : xh0 - 4));
-  const int64_t yp = y == L - 1 ? q0 + Lh - plane : q0 + Lh;
-  const int64_t ym = y == 0 ? q0 - Lh + plane : q0 - Lh;
-  const int64_t zp = z == L - 1 ? q0 + plane - half : q0 + plane;
-  const int64_t zm = z == 0 ? q0 - plane + half : q0 - plane;
+  const int32_t qa = (q0 - xh0) + (odd ? (xh0 + 4 == Lh ? 0 : xh0 + 4) : (xh0 == 0 ? Lh - 4 : xh0 - 4));
+  const int32_t yp = y == L - 1 ? q0 + Lh - (int32_t)plane : q0 + Lh;
+  const int32_t ym = y == 0 ? q0 - Lh + (int32_t)plane : q0 - Lh;
+  const int32_t zp = z == L - 1 ? q0 + (int32_t)plane - (int32_t)half : q0 + (int32_t)plane;
+  const int32_t zm = z == 0 ? q0 - (int32_t)plane + (int32_t)half : q0 - (int32_t)plane;
   const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)colour);
   float4 h4 = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t hb = 0u;
@@ -111,12 +113,14 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
     hb = ld_u32(v.hbit_c + colour * half + q0);
   else
     h4 = __ldg(reinterpret_cast<const float4 *>(v.hh_c + colour * half + q0));
+  uint8_t *self0 = v.spins8 + ((int64_t)r0 * 2 + colour) * half;
+  const uint8_t *O0 = v.spins8 + ((int64_t)r0 * 2 + (colour ^ 1)) * half;
 #pragma unroll
   for (int gg = 0; gg < GT; ++gg) {
     const int r = r0 + gg;
     if (r >= v.R) break;
-    uint8_t *self = v.spins8 + ((int64_t)r * 2 + colour) * half;
-    const uint8_t *O = v.spins8 + ((int64_t)r * 2 + (colour ^ 1)) * half;
+    uint8_t *self = self0 + 2 * half * gg;
+    const uint8_t *O = O0 + 2 * half * gg;
     const uint32_t w0 = ld_u32(O + q0), wa = ld_u32(O + qa);
     const uint32_t wx = odd ? __byte_perm(w0, wa, 0x4321u) : __byte_perm(wa, w0, 0x6543u);
     const uint32_t up = w0 + wx + ld_u32(O + yp) + ld_u32(O + ym) + ld_u32(O + zp) + ld_u32(O + zm);
@@ -154,14 +158,20 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
 }  // namespace
 
 cudaError_t launch_halfsweep_int8(const RealView &v, int colour, uint32_t sweep, cudaStream_t st) {
-  if (v.L % 8 == 0) {
+  if (v.L % 8 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
     constexpr int GT = 4;
     const int64_t groups = (int64_t)v.N / 8;
     const dim3 grid((unsigned)((groups + 255) / 256), (unsigned)((v.R + GT - 1) / GT));
-    if (v.kind == kBimodal)
-      k_halfsweep_int8_rows<true, GT><<<grid, 256, 0, st>>>(v, colour, sweep);
-    else
-      k_halfsweep_int8_rows<false, GT><<<grid, 256, 0, st>>>(v, colour, sweep);
+    const bool bim = v.kind == kBimodal;
+    auto go = [&](auto kb, auto kf) {
+      (bim ? kb : kf)<<<grid, 256, 0, st>>>(v, colour, sweep);
+    };
+    switch (v.L) {
+      case 16: go(k_halfsweep_int8_rows<true, GT, 16>, k_halfsweep_int8_rows<false, GT, 16>); break;
+      case 32: go(k_halfsweep_int8_rows<true, GT, 32>, k_halfsweep_int8_rows<false, GT, 32>); break;
+      case 64: go(k_halfsweep_int8_rows<true, GT, 64>, k_halfsweep_int8_rows<false, GT, 64>); break;
+      default: go(k_halfsweep_int8_rows<true, GT, 0>, k_halfsweep_int8_rows<false, GT, 0>); break;
+    }
     return cudaGetLastError();
   }
   const int64_t total = (int64_t)v.N / 8 * v.R;

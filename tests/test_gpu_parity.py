@@ -79,6 +79,8 @@ def test_random_start_bit_exact(L, layout):
     (16, 32, I8, 20, 5),
     (32, 6, BP, 20, 10),
     (64, 6, BP, 6, 3),        # replica count not a multiple of the cluster's replicas
+    (24, 7, I8, 12, 3),       # word-parallel int8 kernel: L/2 = 12 sites per row, R not a multiple of 4
+    (64, 5, I8, 4, 2),
 ])
 def test_bimodal_trajectory_bit_exact(L, R, layout, sweeps, ex):
     temps = inputs.geometric_temps(1.0, 5.0, R)
