@@ -59,17 +59,23 @@ int words_per_cta(int L, int S) { return L <= 0 || S <= 0 ? 0 : (L / S) * (L * L
 
 using GridFn = void (*)(RealView, GridArgs, uint32_t, int32_t, const float4 *, ExchArgs);
 
-template <int L, int GTI>
+template <int L, int GTI, int NT>
 GridFn grid_pick(bool bim) {
-  return bim ? (GridFn)k_sweeps_grid<L, true, GTI> : (GridFn)k_sweeps_grid<L, false, GTI>;
+  return bim ? (GridFn)k_sweeps_grid<L, true, GTI, NT> : (GridFn)k_sweeps_grid<L, false, GTI, NT>;
 }
 
-// Grid-wide instances: replicas per thread item GT = 4 (one field load per group) or 1.
-GridFn grid_kernel_for(int L, int GT, bool bim) {
-  if (L == 64 && GT == 4) return grid_pick<64, 4>(bim);
-  if (L == 64 && GT == 1) return grid_pick<64, 1>(bim);
-  if (L == 32 && GT == 4) return grid_pick<32, 4>(bim);
-  if (L == 32 && GT == 1) return grid_pick<32, 1>(bim);
+// Grid-wide instances: replicas per thread item GT = 4 (one field load per group), 2 or 1;
+// NT is the launch-bounds thread count (plans may launch fewer threads, in multiples of 32).
+GridFn grid_kernel_for(int L, int GT, int threads, bool bim) {
+  if (threads <= 512) {
+    if (L == 64 && GT == 4) return grid_pick<64, 4, 512>(bim);
+    if (L == 64 && GT == 1) return grid_pick<64, 1, 512>(bim);
+    if (L == 32 && GT == 4) return grid_pick<32, 4, 512>(bim);
+    if (L == 32 && GT == 1) return grid_pick<32, 1, 512>(bim);
+  } else if (threads <= 896) {
+    if (L == 64 && GT == 2) return grid_pick<64, 2, 896>(bim);
+    if (L == 64 && GT == 4) return grid_pick<64, 4, 896>(bim);
+  }
   return nullptr;
 }
 
@@ -177,7 +183,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
     // ignored and the defaults stand
     const bool named = sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4;
-    const bool exists = named && (s == 0 ? (th >= 256 && th <= 512 && th % 32 == 0 && grid_kernel_for(L, gt, bimodal))
+    const bool exists = named && (s == 0 ? (th >= 256 && th <= 1024 && th % 32 == 0 && grid_kernel_for(L, gt, th, bimodal))
                                          : kernel_for(L, s, gt, th, bimodal) != nullptr);
     if (exists) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;
@@ -191,7 +197,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal);
-  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 512 ? grid_kernel_for(L, p.GT, bimodal) : nullptr;
+  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.GT, p.threads, bimodal) : nullptr;
   if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
@@ -305,7 +311,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.ctl = nullptr;
   xa.err = plan.counter + 1;
   if (plan.S == 0) {
-    GridFn gfn = grid_kernel_for(plan.L, plan.GT, v.kind == kBimodal);
+    GridFn gfn = grid_kernel_for(plan.L, plan.GT, plan.threads, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;
     GridArgs ga = grid_args(plan, v.R, plan.sms);
     cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);

@@ -6,13 +6,13 @@
 //
 // The realization's (4-replica group, z plane) units are split evenly over the CTAs
 // (grid_partition.cuh); each CTA keeps its planes of both colours in shared memory for the whole
-// exchange interval.  The z neighbours of a piece's end planes live in other CTAs: after every
-// half-sweep a CTA writes the end planes it just updated to the global lattice and releases its
-// progress word; before touching its own end planes in the next half-sweep it acquires its
-// neighbours' progress words and reads their end planes (L2).  Each half-sweep first processes a
-// whole round of interior planes, so that wait is normally already satisfied.  Waits are bounded
-// (expiry sets the kernel's error word and every later wait returns at once); the kernel always
-// terminates.
+// exchange interval.  The z neighbours of a piece's end planes live in other CTAs.  Each
+// half-sweep updates the end planes first (in the first rounds of thread items), writes them to
+// the global lattice as they are done and releases the CTA's progress word; the interior planes
+// follow.  During the last round, warps without an item acquire the neighbours' progress words
+// and load their end planes (L2) for the next half-sweep, so the neighbours have normally
+// published long before they are needed.  Waits are bounded (expiry sets the kernel's error word
+// and every later wait returns at once); the kernel always terminates.
 #pragma once
 #include <cstdint>
 
@@ -53,8 +53,8 @@ __device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned 
   return false;
 }
 
-template <int L, bool BIM, int GTI>
-__global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
+template <int L, bool BIM, int GTI, int NT>
+__global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
                                                         const float4 *__restrict__ field4, ExchArgs xa) {
   constexpr int PW = L * L / 64, W = L * L * L / 64;
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
   __shared__ Piece pc[kGridMaxPieces];
   __shared__ int np_s, nu_s, nb_s;
   __shared__ int8_t plane_piece[256];
-  __shared__ uint8_t order[256];  // local planes: interior first, then piece end planes
+  __shared__ uint8_t order[256];  // local planes: piece end planes first, then interior
   if (tid == 0) {
     Piece tmp[kGridMaxPieces];
     const int np = grid_pieces(ga.gp, k, tmp);
@@ -75,16 +75,16 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
       nu += tmp[p].n;
     }
     int o = 0;
-    for (int p = 0; p < np; ++p)
-      for (int i = 1; i + 1 < tmp[p].n; ++i) order[o++] = (uint8_t)(tmp[p].lu0 + i);
-    const int nint = o;
     for (int p = 0; p < np; ++p) {
       order[o++] = (uint8_t)tmp[p].lu0;
       if (tmp[p].n > 1) order[o++] = (uint8_t)(tmp[p].lu0 + tmp[p].n - 1);
     }
+    const int nend = o;
+    for (int p = 0; p < np; ++p)
+      for (int i = 1; i + 1 < tmp[p].n; ++i) order[o++] = (uint8_t)(tmp[p].lu0 + i);
     np_s = np;
     nu_s = nu;
-    nb_s = nu - nint;
+    nb_s = nend;
   }
   __syncthreads();
   const int np = np_s, nu = nu_s, nb = nb_s;
@@ -107,13 +107,20 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
 
   constexpr int IPW = PW * (GG / GTI);  // items per plane
   const int items = nu * IPW;
-  const int phase_a = ((nu - nb) * IPW / nt) * nt;  // whole rounds of interior planes
+  // rounds of nt items that hold every end-plane item, and the first item of the last round
+  const int split = min(items, (nb * IPW + nt - 1) / nt * nt);
+  const int last_round = items > split ? split + (items - split - 1) / nt * nt : items;
+  const int warp = tid >> 5, busy_warps = (items - last_round + 31) / 32;
+  const int idle_warps = items > split ? nt / 32 - busy_warps : 0;
   unsigned *err = xa.err;
 
-  // Loads the other colour's end planes of every piece's z neighbours once they have finished
-  // `need` half-sweeps.
-  auto fetch_halos = [&](int other, unsigned need) {
-    if (tid == 0) {
+  // Loads the `other` colour's end planes of every piece's z neighbours once their CTAs have
+  // published `need` half-sweeps: thread `lead` waits, the group of `count` threads (whole warps,
+  // named barrier `bar`) holding it then loads.  The caller makes the loads visible with a CTA
+  // barrier.
+  auto fetch_halos = [&](int other, unsigned need, int t0, int count, int bar) {
+    const int lt = tid - t0;
+    if (lt == 0) {
       for (int p = 0; p < np; ++p) {
         const int64_t base = (int64_t)pc[p].g * L;
         const int klo = grid_owner(ga.gp, base + (pc[p].z0 + L - 1) % L);
@@ -122,15 +129,17 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
         grid_wait(ga.prog, khi, need, err);
       }
     }
-    __syncthreads();
-    for (int t = tid; t < np * 2 * GG * PW; t += nt) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(count) : "memory");
+    for (int t = lt; t < np * 2 * GG * PW; t += count) {
       const int p = t / (2 * GG * PW), side = (t / (GG * PW)) & 1, gg = (t / PW) % GG, w = t % PW;
       const int r = min(pc[p].g * GG + gg, v.R - 1);
       const int z = side ? (pc[p].z0 + pc[p].n) % L : (pc[p].z0 + L - 1) % L;
       halo[t] = __ldcg(v.bits + ((int64_t)r * 2 + other) * W + (int64_t)z * PW + w);
     }
-    __syncthreads();
   };
+  // the neighbours' colour-1 end planes as the launch found them
+  fetch_halos(1, 0u, 0, nt, 1);
+  __syncthreads();
 
   // z-neighbour words (other colour) of local plane lu, word w, replica gg
   auto zn = [&](int lu, int w, int gg, int other, uint32_t &up, uint32_t &dn) {
@@ -148,6 +157,7 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
 #pragma unroll 1
       for (int it = i0 + tid; it < i1; it += nt) {
         const int lu = order[it / IPW], w = it % PW;
+        const bool end_plane = it < nb * IPW;
         const int gb = (it % IPW) / PW * GTI;  // first replica of this item within the group
         const int p = plane_piece[lu];
         const int z = pc[p].z0 + (lu - pc[p].lu0);
@@ -192,29 +202,31 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
         for (int gg = 0; gg < GTI; ++gg) {
           if (gb + gg >= gact) continue;
           if (!BIM) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
-          lat_at(lu, gb + gg, c)[w] = sf[gg] ^ flip[gg];
+          const uint32_t nw = sf[gg] ^ flip[gg];
+          lat_at(lu, gb + gg, c)[w] = nw;
+          if (end_plane) v.bits[((int64_t)(pc[p].g * GG + gb + gg) * 2 + c) * W + wq] = nw;  // publish
         }
       }
     };
-    process(0, phase_a);
-    fetch_halos(other, (unsigned)h);
-    process(phase_a, items);
-    __syncthreads();
-    // publish this half-sweep's end planes (colour c), then the progress word
-    for (int t = tid; t < np * 2 * GG * PW; t += nt) {
-      const int p = t / (2 * GG * PW), side = (t / (GG * PW)) & 1, gg = (t / PW) % GG, w = t % PW;
-      if (gg >= gact_of(p) || (side && pc[p].n == 1)) continue;
-      const int lu = side ? pc[p].lu0 + pc[p].n - 1 : pc[p].lu0;
-      const int r = pc[p].g * GG + gg, z = pc[p].z0 + (lu - pc[p].lu0);
-      v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = lat_at(lu, gg, c)[w];
-    }
-    // the CTA barrier orders every thread's end-plane stores before thread 0's gpu-scope fence
-    // and release (cumulativity), as in a grid-wide barrier
+    // end planes (and the interior items sharing their rounds), then the progress word: the CTA
+    // barrier orders every thread's end-plane stores before thread 0's gpu-scope fence and release
+    // (cumulativity), as in a grid-wide barrier
+    process(0, split);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
       st_release_u32(ga.prog + k, (unsigned)(h + 1));
     }
+    // interior planes; warps without an item in the last round fetch the halos of the next
+    // half-sweep (this colour's end planes of the neighbours), else every thread does afterwards
+    process(split, items);
+    if (idle_warps > 0) {
+      if (warp >= nt / 32 - idle_warps) fetch_halos(c, (unsigned)(h + 1), nt - 32 * idle_warps, 32 * idle_warps, 1);
+    } else {
+      __syncthreads();
+      fetch_halos(c, (unsigned)(h + 1), 0, nt, 1);
+    }
+    __syncthreads();
   }
 
   for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
@@ -226,7 +238,7 @@ __global__ void __launch_bounds__(512, 1) k_sweeps_grid(RealView v, GridArgs ga,
   if (!xa.enabled) return;
 
   // ---- energy partials (Eq. 1) per (replica, piece), then the exchange tail ----------------
-  fetch_halos(1, (unsigned)(2 * nsw));  // final colour-1 end planes of the neighbours
+  // (the halo buffer holds the neighbours' final colour-1 end planes, fetched by the last half-sweep)
   __shared__ long long red_i[3][32];
   __shared__ double red_d[32];
   __shared__ int last_cta;
