@@ -1,7 +1,7 @@
 // Partition of a realization's (replica group, z plane) units over the CTAs of a cooperative
 // launch, for the grid-wide bit-layout sweep (kernels_grid.cuh).  Host and device.
 //
-// Units u = g L + z for replica groups g = 0..NG-1 (4 replicas each) and planes z = 0..L-1.  CTA k
+// Units u = g L + z for replica groups g = 0..NG-1 (of G replicas) and planes z = 0..L-1.  CTA k
 // owns the contiguous units [a_k, a_{k+1}) with a_k = floor(k U / P), U = NG L, P CTAs; its range
 // splits into "pieces" (maximal runs inside one group).  The z neighbours of a piece's first and
 // last planes (periodic in z) belong to the CTAs owner(u) = floor(((u + 1) P - 1) / U).
@@ -10,7 +10,7 @@
 
 namespace rfim {
 
-constexpr int kGridGroup = 4;      // replicas per unit (processed together, one field load each)
+constexpr int kGridGroup = 4;      // default replicas per unit (processed together, one field load each)
 constexpr int kGridMaxPieces = 4;  // pieces per CTA (checked on the host)
 
 struct GridPart {

@@ -59,22 +59,25 @@ int words_per_cta(int L, int S) { return L <= 0 || S <= 0 ? 0 : (L / S) * (L * L
 
 using GridFn = void (*)(RealView, GridArgs, uint32_t, int32_t, const float4 *, ExchArgs);
 
-template <int L, int GTI, int NT>
+template <int L, int GG, int GTI, int NT>
 GridFn grid_pick(bool bim) {
-  return bim ? (GridFn)k_sweeps_grid<L, true, GTI, NT> : (GridFn)k_sweeps_grid<L, false, GTI, NT>;
+  return bim ? (GridFn)k_sweeps_grid<L, true, GG, GTI, NT> : (GridFn)k_sweeps_grid<L, false, GG, GTI, NT>;
 }
 
-// Grid-wide instances: replicas per thread item GT = 4 (one field load per group), 2 or 1;
-// NT is the launch-bounds thread count (plans may launch fewer threads, in multiples of 32).
-GridFn grid_kernel_for(int L, int GT, int threads, bool bim) {
+// Grid-wide instances: G replicas per unit, GT of them per thread item (GT = G: one field load
+// per group); NT is the launch-bounds thread count (plans may launch fewer threads, in multiples
+// of 32).
+GridFn grid_kernel_for(int L, int G, int GT, int threads, bool bim) {
   if (threads <= 512) {
-    if (L == 64 && GT == 4) return grid_pick<64, 4, 512>(bim);
-    if (L == 64 && GT == 1) return grid_pick<64, 1, 512>(bim);
-    if (L == 32 && GT == 4) return grid_pick<32, 4, 512>(bim);
-    if (L == 32 && GT == 1) return grid_pick<32, 1, 512>(bim);
+    if (L == 64 && G == 4 && GT == 4) return grid_pick<64, 4, 4, 512>(bim);
+    if (L == 64 && G == 4 && GT == 1) return grid_pick<64, 4, 1, 512>(bim);
+    if (L == 64 && G == 8 && GT == 8) return grid_pick<64, 8, 8, 512>(bim);
+    if (L == 64 && G == 8 && GT == 4) return grid_pick<64, 8, 4, 512>(bim);
+    if (L == 32 && G == 4 && GT == 4) return grid_pick<32, 4, 4, 512>(bim);
+    if (L == 32 && G == 4 && GT == 1) return grid_pick<32, 4, 1, 512>(bim);
   } else if (threads <= 896) {
-    if (L == 64 && GT == 2) return grid_pick<64, 2, 896>(bim);
-    if (L == 64 && GT == 4) return grid_pick<64, 4, 896>(bim);
+    if (L == 64 && G == 4 && GT == 2) return grid_pick<64, 4, 2, 896>(bim);
+    if (L == 64 && G == 4 && GT == 4) return grid_pick<64, 4, 4, 896>(bim);
   }
   return nullptr;
 }
@@ -85,7 +88,7 @@ constexpr size_t kGridMinSmem = 116 * 1024;  // more than half an SM's shared me
 GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
   GridArgs ga{};
   ga.gp.L = p.L;
-  ga.gp.NG = (R + kGridGroup - 1) / kGridGroup;
+  ga.gp.NG = (R + p.G - 1) / p.G;
   ga.gp.U = (int64_t)ga.gp.NG * p.L;
   int64_t P = std::min<int64_t>(sms, ga.gp.U / 3);
   if (P < 1) P = 1;
@@ -104,10 +107,10 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
   return ga;
 }
 
-size_t grid_smem(int L, int max_units) {
+size_t grid_smem(int L, int G, int max_units) {
   const size_t PW = (size_t)L * L / 64;
-  const size_t need = (size_t)max_units * kGridGroup * 2 * PW * 4 + (size_t)kGridMaxPieces * 2 * kGridGroup * PW * 4 +
-                      tab_bytes(kGridMaxPieces * kGridGroup);
+  const size_t need = (size_t)max_units * G * 2 * PW * 4 + (size_t)kGridMaxPieces * 2 * G * PW * 4 +
+                      tab_bytes(kGridMaxPieces * G);
   return std::max(need, kGridMinSmem);
 }
 
@@ -183,7 +186,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
     // ignored and the defaults stand
     const bool named = sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4;
-    const bool exists = named && (s == 0 ? (th >= 256 && th <= 1024 && th % 32 == 0 && grid_kernel_for(L, gt, th, bimodal))
+    const bool exists = named && (s == 0 ? (th >= 256 && th <= 1024 && th % 32 == 0 && grid_kernel_for(L, g, gt, th, bimodal))
                                          : kernel_for(L, s, gt, th, bimodal) != nullptr);
     if (exists) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;
@@ -197,13 +200,12 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal);
-  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.GT, p.threads, bimodal) : nullptr;
+  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.G, p.GT, p.threads, bimodal) : nullptr;
   if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
   }
   if (gfn) {
-    p.G = kGridGroup;
     p.sms = sms;
     // largest partition over every R the context can reach
     int maxu = 0;
@@ -215,7 +217,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
       if (err) *err = "grid plan: too many planes per CTA";
       return -1;
     }
-    p.smem = grid_smem(L, maxu);
+    p.smem = grid_smem(L, p.G, maxu);
   }
   if (!gfn)
     p.smem = p.threads == kWsThreads ? ws_smem(L, p.S, p.G)
@@ -311,7 +313,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.ctl = nullptr;
   xa.err = plan.counter + 1;
   if (plan.S == 0) {
-    GridFn gfn = grid_kernel_for(plan.L, plan.GT, plan.threads, v.kind == kBimodal);
+    GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;
     GridArgs ga = grid_args(plan, v.R, plan.sms);
     cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);

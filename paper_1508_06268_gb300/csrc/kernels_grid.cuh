@@ -53,12 +53,11 @@ __device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned 
   return false;
 }
 
-template <int L, bool BIM, int GTI, int NT>
+template <int L, bool BIM, int GG, int GTI, int NT>
 __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
                                                         const float4 *__restrict__ field4, ExchArgs xa) {
   constexpr int PW = L * L / 64, W = L * L * L / 64;
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
-  constexpr int GG = kGridGroup;
   extern __shared__ __align__(16) uint32_t sm[];
   const int k = blockIdx.x, nt = blockDim.x, tid = threadIdx.x;
   __shared__ Piece pc[kGridMaxPieces];

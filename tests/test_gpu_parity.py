@@ -350,7 +350,8 @@ def test_warp_specialised_variant_matches(kind, monkeypatch):
 
 @pytest.mark.parametrize("L,R,plan", [(64, 6, "0,4,4,512"), (64, 70, "0,4,4,512"), (32, 64, "0,4,4,512"),
                                        (64, 6, "0,4,1,512"), (64, 70, "0,4,1,512"), (32, 64, "0,4,1,384"),
-                                       (64, 70, "0,4,2,896"), (64, 13, "0,4,2,896")])
+                                       (64, 70, "0,4,2,896"), (64, 13, "0,4,2,896"), (64, 70, "0,8,8,512"),
+                                       (64, 21, "0,8,4,512")])
 def test_grid_wide_variant_bit_exact(L, R, plan, monkeypatch):
     """The cooperative grid-wide plans (shape 0,4,GT,threads: replica groups x z planes over one
     CTA per SM, halos through L2, GT replicas per thread item) against the oracle, bimodal field,
@@ -366,7 +367,7 @@ def test_grid_wide_variant_bit_exact(L, R, plan, monkeypatch):
     np.testing.assert_array_equal(g.observables()["sums"], o.observables())
 
 
-@pytest.mark.parametrize("plan", ["0,4,4,512", "0,4,1,512", "0,4,2,896"])
+@pytest.mark.parametrize("plan", ["0,4,4,512", "0,4,1,512", "0,4,2,896", "0,8,8,512"])
 def test_grid_wide_variant_gaussian_matches_cluster_plan(plan, monkeypatch):
     """Gaussian field: the grid-wide plans take the same decisions as the default cluster plan
     (spins and permutation identical; energies summed over other slab boundaries agree to
