@@ -257,6 +257,15 @@ int rfim_selftest_bits(int32_t L, uint32_t seed);
    the number of violations (0 = pass) or -1 for invalid arguments. */
 int rfim_selftest_grid(int32_t L, int32_t R, int32_t P);
 
+/* Device self-test of the bounded waits that the grid-wide kernel uses between CTAs (the paper
+   has no counterpart: its CTAs never wait on one another).  One thread waits for a progress word
+   that nothing sets (set_flag = 0) or that is already set (set_flag = 1), for at most spin_limit
+   polls (1 <= spin_limit <= 2^22, each poll followed by a 64 ns sleep).  Returns RFIM_ETIMEOUT when
+   the wait expired (the kernel recorded it in its error word and returned), RFIM_OK when the flag
+   was seen, RFIM_EINVAL for a bad spin_limit, RFIM_ECUDA on a CUDA error.  Synchronous on the
+   default stream; the context of the calling thread stays usable after an expiry. */
+int rfim_selftest_wait(int32_t spin_limit, int32_t set_flag);
+
 #ifdef __cplusplus
 }
 #endif

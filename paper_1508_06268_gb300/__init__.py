@@ -101,6 +101,7 @@ def load():
             L.rfim_server_last_error.restype = C.c_char_p
             L.rfim_exchange_noalloc.argtypes = [C.POINTER(ExchangeBuffers), u32, i64, P]
             L.rfim_selftest_grid.argtypes = [i32, i32, i32]
+            L.rfim_selftest_wait.argtypes = [i32, i32]
             L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
@@ -109,7 +110,7 @@ def load():
                          "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
                          "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
                          "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
-                         "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid"):
+                         "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid", "rfim_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -150,6 +151,11 @@ def selftest_grid(L: int, R: int, P: int) -> int:
 
 def selftest_bits(L: int, seed: int = 1) -> int:
     return load().rfim_selftest_bits(L, seed)
+
+
+def selftest_wait(spin_limit: int, set_flag: bool) -> int:
+    """Status of one bounded device wait on a flag that is unset (expires) or set."""
+    return load().rfim_selftest_wait(spin_limit, 1 if set_flag else 0)
 
 
 class Realization:

@@ -419,6 +419,29 @@ extern "C" int rfim_selftest_bits(int32_t L, uint32_t seed) {
 
 // Host self-check of the grid-wide partition: every unit has exactly one owner consistent with
 // the CTA ranges, pieces tile each range inside single groups, at most kGridMaxPieces per CTA.
+namespace {
+// words[0]: progress word, words[1]: error word
+__global__ void k_selftest_wait(unsigned *words, unsigned limit) {
+  if (threadIdx.x == 0) rfim::grid_wait(words, 0, 1u, words + 1, limit);
+}
+}  // namespace
+
+extern "C" int rfim_selftest_wait(int32_t spin_limit, int32_t set_flag) {
+  if (spin_limit < 1 || spin_limit > (int32_t)rfim::kGridSpinLimit) return -1;  // RFIM_EINVAL
+  unsigned *d = nullptr;
+  unsigned h[2] = {set_flag ? 1u : 0u, 0u};
+  if (cudaMalloc(&d, sizeof h) != cudaSuccess) return -3;  // RFIM_ECUDA
+  cudaError_t e = cudaMemcpy(d, h, sizeof h, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_selftest_wait<<<1, 32>>>(d, (unsigned)spin_limit);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return -3;  // RFIM_ECUDA
+  return h[1] ? -4 : 0;             // RFIM_ETIMEOUT : RFIM_OK
+}
+
 extern "C" int rfim_selftest_grid(int32_t L, int32_t R, int32_t P) {
   using namespace rfim;
   if (L < 2 || R < 2 || P < 1) return -1;

@@ -43,8 +43,9 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
 }
 
 // Bounded wait for prog[k] >= need; false on expiry (which is recorded) or an earlier expiry.
-__device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned need, unsigned *err) {
-  for (unsigned it = 0; it < kGridSpinLimit; ++it) {
+__device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned need, unsigned *err,
+                                          unsigned limit = kGridSpinLimit) {
+  for (unsigned it = 0; it < limit; ++it) {
     if (ld_acquire_u32(prog + k) >= need) return true;
     if (*(volatile unsigned *)err) return false;
     __nanosleep(64);

@@ -385,3 +385,19 @@ def test_grid_wide_variant_gaussian_matches_cluster_plan(plan, monkeypatch):
     np.testing.assert_array_equal(a["spins"], b["spins"])
     np.testing.assert_array_equal(a["t2r"], b["t2r"])
     np.testing.assert_allclose(ref.observables()["sums"], grid.observables()["sums"], rtol=1e-12)
+
+
+def test_bounded_wait_expires_and_context_stays_usable():
+    """A device wait on a flag that nothing sets gives up after its poll limit and reports
+    RFIM_ETIMEOUT; a set flag passes; afterwards the context still runs the sweep kernels."""
+    import time
+    t0 = time.perf_counter()
+    assert rf.selftest_wait(2000, False) == rf.ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert rf.selftest_wait(2000, True) == rf.OK
+    assert rf.selftest_wait(0, True) == rf.EINVAL
+    temps = inputs.geometric_temps(1.0, 5.0, 6)
+    g, o = make_pair(16, temps, kind=BIM, layout=BP, h=1.5, field_seed=2, seed=9)
+    g.run(10, 5, 0)
+    o.run(10, 5, 0)
+    assert_same_state(g, o, "after an expired wait")
