@@ -43,6 +43,8 @@ KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
   RFIM_BITS_INSTANCE(32, 1, 1, 512)
   RFIM_BITS_INSTANCE(32, 1, 2, 512)
   RFIM_BITS_INSTANCE(32, 2, 1, 512)
+  RFIM_BITS_INSTANCE(32, 2, 1, 256)
+  RFIM_BITS_INSTANCE(32, 4, 1, 128)
   RFIM_BITS_INSTANCE(16, 1, 1, 512)
   RFIM_BITS_INSTANCE(8, 1, 1, 128)
   RFIM_BITS_INSTANCE(8, 1, 1, 512)
@@ -145,7 +147,7 @@ void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &
 std::vector<std::string> plan_candidates(int32_t L) {
   if (L == 64)
     return {"4,4,4,512", "0,4,4,512", "0,4,1,512", "4,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
-  if (L == 32) return {"1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512", "0,4,1,512"};
+  if (L == 32) return {"2,1,1,256", "4,1,1,128", "1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512", "0,4,1,512"};
   if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
   return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
 }
@@ -166,7 +168,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
       p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
     }
   } else if (L == 32) {
-    p.S = 1; p.G = 1; p.GT = 1; p.threads = 512;
+    p.S = 2; p.G = 1; p.GT = 1; p.threads = 256;  // two z slabs per replica, one word per thread
   } else if (L == 16) {
     p.S = 1; p.G = 8; p.GT = 1; p.threads = 512;
   } else {
