@@ -239,12 +239,13 @@ int rfim_profile_read(rfim_ctx *ctx, double *sweep_ms, int64_t *sweep_launches, 
                       int64_t *exchange_launches);
 
 /* Launch-shape tuner for the bit layout.  Times every instantiated launch shape (cluster size S
-   = z slabs per replica group, replicas G per cluster, replicas GT per thread, threads per CTA) on
-   a scratch realization with this L, R and field kind (20-50 exchange intervals of 10 sweeps
-   each, CUDA-event timing) and remembers the fastest: later rfim_create calls in this process with
-   the same L, R_capacity and field kind use it.  plan_out (optional, plan_cap chars) receives
-   "S,G,GT,threads"; *attempts_per_ns (optional) the best rate.  Synchronous; allocates scratch
-   realizations.  Errors: RFIM_EINVAL (unsupported L, R < 2), RFIM_ECUDA. */
+   = z slabs per replica group, replicas G per cluster, replicas GT per thread, threads per CTA;
+   S = 0 is the grid-wide cooperative plan with one CTA per SM, G replicas per (group, z plane)
+   unit) on a scratch realization with this L, R and field kind (20-50 exchange intervals of 10
+   sweeps each, CUDA-event timing) and remembers the fastest: later rfim_create calls in this
+   process with the same L, R_capacity and field kind use it.  plan_out (optional, plan_cap chars)
+   receives "S,G,GT,threads"; *attempts_per_ns (optional) the best rate.  Synchronous; allocates
+   scratch realizations.  Errors: RFIM_EINVAL (unsupported L, R < 2), RFIM_ECUDA. */
 int rfim_tune(int32_t L, int32_t R, int32_t field_kind, char *plan_out, int32_t plan_cap, double *attempts_per_ns);
 
 /* Host-only self-check of the bit layout's word-level neighbour arithmetic (multi-spin coding,
@@ -253,7 +254,7 @@ int rfim_tune(int32_t L, int32_t R, int32_t field_kind, char *plan_out, int32_t 
 int rfim_selftest_bits(int32_t L, uint32_t seed);
 
 /* Host-only self-check of the partition used by the grid-wide bit-layout kernel (replica groups
-   of 4 x z planes spread over P CTAs): unique owners, pieces tiling every CTA's range.  Returns
+   of 4 x z planes spread over P CTAs; other group sizes partition the same way): unique owners, pieces tiling every CTA's range.  Returns
    the number of violations (0 = pass) or -1 for invalid arguments. */
 int rfim_selftest_grid(int32_t L, int32_t R, int32_t P);
 
