@@ -19,6 +19,10 @@
 
 namespace rfim {
 
+#ifndef RFIM_INT8_GT
+#define RFIM_INT8_GT 4
+#endif
+
 namespace {
 
 template <bool kBimodalField>
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
 
 cudaError_t launch_halfsweep_int8(const RealView &v, int colour, uint32_t sweep, cudaStream_t st) {
   if (v.L % 8 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
-    constexpr int GT = 4;
+    constexpr int GT = RFIM_INT8_GT;
     const int64_t groups = (int64_t)v.N / 8;
     const dim3 grid((unsigned)((groups + 255) / 256), (unsigned)((v.R + GT - 1) / GT));
     const bool bim = v.kind == kBimodal;
