@@ -83,6 +83,10 @@ def lib():
             L.orc_get_exchange_stats.argtypes = [P, P, P]
             L.orc_get_energies.argtypes = [P, P, P]
             L.orc_get_obs.argtypes = [P, P]
+            L.orc_get_obsF.argtypes = [P, P]
+            L.orc_set_measure_xi.argtypes = [P, i32]
+            L.orc_structure_F.argtypes = [P, i32]
+            L.orc_structure_F.restype = f64
             L.orc_bimodal_threshold.argtypes = [f64, f64]
             L.orc_bimodal_threshold.restype = C.c_uint64
             _lib = L
@@ -244,3 +248,55 @@ class Oracle:
         obs = np.zeros((self.R, 5), dtype=np.float64)
         self._lib.orc_get_obs(self._h, _ptr(obs))
         return obs
+
+    def set_measure_xi(self, on: bool):
+        self._lib.orc_set_measure_xi(self._h, 1 if on else 0)
+
+    def structure_F(self, r: int) -> float:
+        return self._lib.orc_structure_F(self._h, r)
+
+    def observables_F(self):
+        F = np.zeros(self.R, dtype=np.float64)
+        self._lib.orc_get_obsF(self._h, _ptr(F))
+        return F
+
+
+# ---- derived observables of Sec. 7 --------------------------------------------------------------
+# Readings: C = (N / T^2)(<e^2> - <e>^2) with e the energy per site (the printed L^3 prefactor);
+# xi = sqrt(N <m^2> / <F> - 1): the printed <M^2> taken as the zero-wave-number structure factor
+# (1/N) <(sum_i s_i)^2> = N <m^2>, which has F's normalisation; no 1/(2 sin(K/2)) factor, as printed.
+
+THERMAL_COLUMNS = ("e", "C", "absm", "m2", "m4", "F", "xi")
+
+
+def thermal(obs, F, n_meas, N, T):
+    """Per-temperature thermal averages of one realization: array [R][7] in THERMAL_COLUMNS order
+    from the accumulator sums obs[R][5] (e, e^2, |m|, m^2, m^4) and F[R] (None: F and xi are NaN)."""
+    obs = np.asarray(obs, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    R = obs.shape[0]
+    out = np.full((R, 7), np.nan)
+    if n_meas <= 0:
+        return out
+    avg = obs / float(n_meas)
+    out[:, 0] = avg[:, 0]
+    out[:, 1] = float(N) / (T * T) * (avg[:, 1] - avg[:, 0] * avg[:, 0])
+    out[:, 2:5] = avg[:, 2:5]
+    if F is not None:
+        Fa = np.asarray(F, dtype=np.float64) / float(n_meas)
+        out[:, 5] = Fa
+        arg = float(N) * avg[:, 3] / Fa - 1.0
+        out[:, 6] = np.where(arg >= 0.0, np.sqrt(np.maximum(arg, 0.0)), np.nan)
+    return out
+
+
+DISORDER_COLUMNS = ("e", "C", "absm", "xi", "g")
+
+
+def disorder_average(thermals):
+    """Averages over realizations (Sec. 7, [.]) of per-realization thermal arrays sharing one
+    temperature set: [e], [C], [|m|], [xi] and the Binder factor [g] = (3 - [<m^4>] / [<m^2>]^2) / 2."""
+    t = np.stack([np.asarray(a, dtype=np.float64) for a in thermals])
+    mean = t.mean(axis=0)
+    g = 0.5 * (3.0 - mean[:, 4] / (mean[:, 3] * mean[:, 3]))
+    return np.stack([mean[:, 0], mean[:, 1], mean[:, 2], mean[:, 6], g], axis=1)

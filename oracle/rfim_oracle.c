@@ -16,7 +16,10 @@
  *   - Eq. 3 (alternator A = (x+y+z) mod 2): plain checkerboard, colour 0 then colour 1.
  *   - Sec. 3.3: temperatures are swapped, not lattices (t2r = "trs", r2t = "rts").
  *   - Sec. 4: adaptive temperature set, midpoint insertion at the a lowest exchange rates.
- *   - Sec. 7, Eqs. 11-12: per-temperature accumulators of e, e^2, |m|, m^2, m^4.
+ *   - Sec. 7, Eqs. 11-12: per-temperature accumulators of e, e^2, |m|, m^2, m^4, and (when
+ *     enabled) of the structure factor F of the correlation-length formula, with the spins s_i
+ *     in place of the printed h_i: F = (F1 + F2) / (3 L^3), F1 = sum over the axes d of
+ *     (sum_i s_i cos(K i_d))^2, F2 the same with sin, K = 2 pi / L.
  *
  * Random numbers (the paper names no generator): Philox4x32-10 from its published definition
  * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
@@ -117,6 +120,8 @@ typedef struct {
   double *E;       /* [Rcap] energy of replica r at the last exchange step */
   int64_t *M;      /* [Rcap] magnetisation sum of replica r at the last exchange step */
   double *obs;     /* [Rcap][5] sums of e, e^2, |m|, m^2, m^4 per temperature index */
+  double *obsF;    /* [Rcap] sums of the structure factor F per temperature index */
+  int32_t measure_xi;
   int64_t n_meas;
   int64_t sweep;   /* global sweep counter (0-based) */
   int64_t xstep;   /* global exchange step counter j (0-based) */
@@ -167,7 +172,7 @@ static void rebuild_thresholds(orc_t *o) {
 void orc_destroy(orc_t *o) {
   if (!o) return;
   free(o->T); free(o->hraw); free(o->hh); free(o->s); free(o->t2r); free(o->r2t);
-  free(o->att); free(o->acc); free(o->E); free(o->M); free(o->obs); free(o->thr);
+  free(o->att); free(o->acc); free(o->E); free(o->M); free(o->obs); free(o->obsF); free(o->thr);
   free(o);
 }
 
@@ -197,6 +202,7 @@ orc_t *orc_create(int32_t L, int32_t R, int32_t Rcap, float J, float h, int32_t 
   o->E = (double *)calloc(Rcap, sizeof(double));
   o->M = (int64_t *)calloc(Rcap, sizeof(int64_t));
   o->obs = (double *)calloc((size_t)Rcap * 5, sizeof(double));
+  o->obsF = (double *)calloc((size_t)Rcap, sizeof(double));
   o->thr = (uint64_t *)calloc((size_t)Rcap * 26, sizeof(uint64_t));
   memcpy(o->T, temps, sizeof(double) * R);
   if (field_kind == ORC_FIELD_EXPLICIT) {
@@ -225,6 +231,7 @@ void orc_reset(orc_t *o, uint32_t stage) {
     o->t2r[k] = k; o->r2t[k] = k; o->att[k] = 0; o->acc[k] = 0; o->E[k] = 0.0; o->M[k] = 0;
   }
   memset(o->obs, 0, sizeof(double) * 5 * o->Rcap);
+  memset(o->obsF, 0, sizeof(double) * o->Rcap);
   o->n_meas = 0; o->sweep = 0; o->xstep = 0;
 }
 
@@ -323,6 +330,35 @@ double orc_energy(const orc_t *o, int32_t r, int64_t *B_out, double *F_out, int6
   return -(double)o->J * (double)B - F;
 }
 
+/* Structure factor of replica r at the smallest nonzero wave number (Sec. 7, correlation
+   length; s_i read for the printed h_i): F = (F1 + F2) / (3 L^3) with F1 = sum over the three
+   axes d of (sum_i s_i cos(K i_d))^2 and F2 the same with sin, K = 2 pi / L.  Direct sums over
+   the sites in natural order, in double. */
+double orc_structure_F(const orc_t *o, int32_t r) {
+  const int32_t L = o->L;
+  const double K = 2.0 * 3.14159265358979323846 / (double)L;
+  const int8_t *s = o->s + (int64_t)r * o->N;
+  double c[3] = {0.0, 0.0, 0.0}, sn[3] = {0.0, 0.0, 0.0};
+  for (int32_t z = 0; z < L; ++z)
+    for (int32_t y = 0; y < L; ++y)
+      for (int32_t x = 0; x < L; ++x) {
+        const double si = (double)s[site_index(L, x, y, z)];
+        const int32_t xyz[3] = {x, y, z};
+        for (int d = 0; d < 3; ++d) {
+          c[d] += si * cos(K * (double)xyz[d]);
+          sn[d] += si * sin(K * (double)xyz[d]);
+        }
+      }
+  double F1 = 0.0, F2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    F1 += c[d] * c[d];
+    F2 += sn[d] * sn[d];
+  }
+  return (F1 + F2) / (3.0 * (double)o->N);
+}
+
+void orc_set_measure_xi(orc_t *o, int32_t on) { o->measure_xi = on ? 1 : 0; }
+
 /* One exchange step j (Eq. 2 with W = min(1, e^Delta); pairs k = j mod 2, j mod 2 + 2, ...,
    temperatures swapped through t2r / r2t as in Sec. 3.3), then the measurement of Sec. 7
    when j >= measure_from. */
@@ -351,6 +387,7 @@ void orc_exchange(orc_t *o, int64_t measure_from) {
       double m = (double)o->M[a] / (double)o->N;
       double *acc = o->obs + (int64_t)k * 5;
       acc[0] += e; acc[1] += e * e; acc[2] += fabs(m); acc[3] += m * m; acc[4] += m * m * m * m;
+      if (o->measure_xi) o->obsF[k] += orc_structure_F(o, a);
     }
     o->n_meas += 1;
   }
@@ -467,5 +504,6 @@ void orc_get_energies(const orc_t *o, double *E, int64_t *M) {
   if (M) memcpy(M, o->M, sizeof(int64_t) * o->R);
 }
 void orc_get_obs(const orc_t *o, double *obs) { memcpy(obs, o->obs, sizeof(double) * 5 * o->R); }
+void orc_get_obsF(const orc_t *o, double *F) { memcpy(F, o->obsF, sizeof(double) * o->R); }
 /* Bimodal threshold used for an energy change dE at inverse temperature beta (tests). */
 uint64_t orc_bimodal_threshold(double beta, double dE) { return bimodal_threshold(beta, dE); }

@@ -51,3 +51,23 @@ def colour_of(L: int) -> np.ndarray:
 
 def permutations_of(R: int):
     return [tuple(p) for p in itertools.permutations(range(R))]
+
+
+def structure_factor_fft(spins: np.ndarray, L: int) -> float:
+    """F of the correlation-length formula by numpy FFTs of the three marginals: the wave number
+    2 pi / L component of each axis' marginal, squared modulus, averaged over axes, per site."""
+    s = np.asarray(spins, dtype=np.float64).reshape(L, L, L)  # [z][y][x]
+    total = 0.0
+    for axes in ((0, 1), (0, 2), (1, 2)):  # keep x, y, z in turn
+        marginal = s.sum(axis=axes)
+        total += abs(np.fft.fft(marginal)[1]) ** 2
+    return total / (3.0 * L ** 3)
+
+
+def exact_energy_moments(L: int, J: float, hh: np.ndarray, beta: float):
+    """Exact <E> and <E^2> (total energy) by enumeration."""
+    states = all_states(L ** 3)
+    E = np.array([energy(s, L, J, hh) for s in states])
+    w = np.exp(-beta * (E - E.min()))
+    w /= w.sum()
+    return float(np.dot(w, E)), float(np.dot(w, E * E))

@@ -402,3 +402,95 @@ def test_adaptation_rejects_over_capacity():
     o = Oracle(4, temps, field_kind=FIELD_BIMODAL, R_capacity=6)
     with pytest.raises(ValueError):
         o.adapt(2, 10, 5, 2)
+
+
+# ------------------------------------------------------------ Sec. 7 observables beyond e and m
+@pytest.mark.parametrize("L", [2, 4, 6, 8])
+def test_structure_factor_matches_fft_of_marginals(L):
+    rng = np.random.default_rng(L)
+    R = 3
+    o = Oracle(L, inputs.geometric_temps(1.0, 3.0, R), field_kind=FIELD_BIMODAL, seed=5)
+    s = rng.choice(np.array([-1, 1], dtype=np.int8), size=(R, L ** 3))
+    o.set_spins(s)
+    for r in range(R):
+        assert o.structure_F(r) == pytest.approx(brute.structure_factor_fft(s[r], L), rel=1e-12, abs=1e-12)
+
+
+def test_structure_factor_of_uniform_and_staggered_lattices():
+    L = 8
+    o = Oracle(L, [1.0, 2.0], field_kind=FIELD_BIMODAL)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    up = np.ones(L ** 3, dtype=np.int8)
+    stripes = np.where(np.cos(2 * np.pi * x / L) >= 0, 1, -1).astype(np.int8).reshape(-1)  # half-period slabs in x
+    o.set_spins(np.stack([up, stripes]))
+    assert abs(o.structure_F(0)) < 1e-20  # a full period of cos and sin sums to zero
+    # slabs along x: only the x axis contributes, |sum_x s(x) e^{iKx}|^2 L^4 / (3 L^3)
+    sx = np.where(np.cos(2 * np.pi * np.arange(L) / L) >= 0, 1.0, -1.0)
+    want = abs(np.sum(sx * np.exp(2j * np.pi * np.arange(L) / L))) ** 2 * L ** 4 / (3 * L ** 3)
+    assert o.structure_F(1) == pytest.approx(want, rel=1e-12)
+
+
+def test_structure_factor_accumulates_lattice_at_each_temperature():
+    L, R = 4, 3
+    o = Oracle(L, inputs.geometric_temps(1.0, 4.0, R), field_kind=FIELD_BIMODAL, h=1.2, seed=9)
+    o.set_measure_xi(True)
+    want = np.zeros(R)
+    for _ in range(12):
+        o.run(1, 1, 0)  # one sweep, then an exchange step with its measurement
+        t2r, _ = o.perm()
+        s = o.spins()
+        want += [brute.structure_factor_fft(s[t2r[k]], L) for k in range(R)]
+    np.testing.assert_allclose(o.observables_F(), want, rtol=1e-12)
+    assert o.n_meas == 12
+
+
+def test_specific_heat_equals_temperature_derivative_of_energy():
+    """C = (N / T^2)(<e^2> - <e>^2) from accumulator sums equals d<e>/dT, the specific heat per
+    site (fluctuation-dissipation; exact 2x2x2 enumeration)."""
+    L, J = 2, 1.0
+    hh = brute.scaled_field(1.0, np.where(np.arange(8) % 3 == 0, 1.0, -1.0))
+    N = L ** 3
+    for T in (1.5, 3.0, 6.0):
+        E1, E2 = brute.exact_energy_moments(L, J, hh, 1.0 / T)
+        n = 1000
+        obs = np.array([[n * E1 / N, n * E2 / N ** 2, 0.0, 0.0, 0.0]])
+        C = oracle.thermal(obs, None, n, N, np.array([T]))[0, 1]
+        dT = 1e-4 * T
+        ep = brute.exact_energy_moments(L, J, hh, 1.0 / (T + dT))[0] / N
+        em = brute.exact_energy_moments(L, J, hh, 1.0 / (T - dT))[0] / N
+        assert C == pytest.approx((ep - em) / (2 * dT), rel=1e-6)
+
+
+def test_binder_factor_limits():
+    """g = 1 for a magnetisation of fixed modulus, g -> 0 for a Gaussian one (textbook limits)."""
+    rng = np.random.default_rng(3)
+    n, N = 20000, 64
+    T = np.array([1.0])
+
+    def sums(m):
+        return np.array([[0.0, 0.0, np.abs(m).sum(), (m ** 2).sum(), (m ** 4).sum()]])
+
+    ordered = oracle.thermal(sums(rng.choice([-1.0, 1.0], size=n)), None, n, N, T)
+    gauss = oracle.thermal(sums(rng.normal(0.0, 0.1, size=n)), None, n, N, T)
+    avg = oracle.disorder_average([ordered, ordered])
+    assert avg[0, 4] == pytest.approx(1.0, abs=1e-12)
+    assert abs(oracle.disorder_average([gauss])[0, 4]) < 0.05
+
+
+def test_correlation_length_vanishes_for_independent_spins():
+    """Independent +-1 spins (beta = 0): N <m^2> = <F> = 1, so xi = 0; measured on sampled
+    lattices through the oracle's own F and magnetisation."""
+    rng = np.random.default_rng(11)
+    L, R, n = 6, 2, 400
+    o = Oracle(L, [1.0, 2.0], field_kind=FIELD_BIMODAL)
+    m2 = F = 0.0
+    for _ in range(n):
+        s = rng.choice(np.array([-1, 1], dtype=np.int8), size=(R, L ** 3))
+        o.set_spins(s)
+        m2 += (s[0].astype(np.float64).mean()) ** 2
+        F += o.structure_F(0)
+    N = L ** 3
+    assert N * m2 / n == pytest.approx(1.0, abs=0.15)
+    assert F / n == pytest.approx(1.0, abs=0.15)
+    xi = oracle.thermal(np.array([[0.0, 0.0, 0.0, m2, 0.0]]), np.array([F]), n, N, np.array([1.0]))[0, 6]
+    assert np.isnan(xi) or xi < 0.5
