@@ -124,16 +124,44 @@ int rfim_adapt_temps(rfim_ctx *ctx, int32_t n_trials, int64_t sweeps_per_trial, 
 
 /* Observables: caller-owned host arrays sized for R (= the context's current R); any pointer may
    be NULL.  sums[k] are over the n_meas measurements at temperature index k (Sec. 7):
-   e = E/N, e^2, |m|, m^2, m^4 with m = M/N.  att/acc have R-1 entries (pair k, k+1).
-   Synchronous. */
+   e = E/N, e^2, |m|, m^2, m^4 with m = M/N, and F, the structure factor of the correlation length
+   (zeros unless rfim_set_measure_xi enabled it; always zeros in served results).  att/acc have
+   R-1 entries (pair k, k+1).  Synchronous. */
 typedef struct {
   int32_t R;        /* out: current number of replicas */
   double *T;        /* [R] temperatures */
   double *e, *e2, *absm, *m2, *m4; /* [R] sums */
   uint64_t *att, *acc;             /* [R-1] */
   int64_t n_meas;   /* out */
+  double *F;        /* [R] sums of the structure factor F (see rfim_set_measure_xi) */
 } rfim_obs;
 int rfim_observables(rfim_ctx *ctx, rfim_obs *out);
+
+/* Enables (on != 0) or disables the measurement of the structure factor that the correlation
+   length of Sec. 7 needs, read with the spins s_i for the printed h_i:
+   F = (F1 + F2) / (3 L^3), F1 = sum over the axes d of (sum_i s_i cos(K i_d))^2, F2 the same with
+   sin, K = 2 pi / L.  When enabled, every measuring exchange step (j >= measure_from) adds each
+   replica's F to the sum of its temperature index, one extra launch per step.  Enable it before the
+   first measurement (RFIM_ESTATE otherwise); rfim_adapt_temps and restarts clear the sums with the
+   other accumulators.  Synchronous. */
+int rfim_set_measure_xi(rfim_ctx *ctx, int32_t on);
+
+/* Thermal averages of one realization (Sec. 7) from its accumulators (obs as filled by
+   rfim_observables or rfim_server_poll; T, e, e2, absm, m2, m4 required, F optional), for a lattice
+   of N = L^3 sites.  out: host double[R][7] per temperature index k:
+   <e>, C = (N / T_k^2)(<e^2> - <e>^2) (e the energy per site, the printed L^3 prefactor),
+   <|m|>, <m^2>, <m^4>, <F>, xi = sqrt(N <m^2> / <F> - 1) (the printed <M^2> taken as the
+   zero-wave-number structure factor N <m^2>, which has F's normalisation; no 1/(2 sin(K/2))
+   factor, as printed; +infinity when <F> < 1e-20, i.e. a uniform lattice at every measurement).
+   NaN where undefined (no measurements, no F, negative radicand).
+   Host only; RFIM_EINVAL for missing arrays or N < 1. */
+int rfim_thermal(const rfim_obs *obs, int32_t N, double *out);
+
+/* Disorder average [.] of Sec. 7 over n realizations that share one temperature set: thermals is
+   host double[n][R][7] (rfim_thermal's rows, realization-major), out host double[R][5] per
+   temperature index: [<e>], [C], [<|m|>], [xi], and the Binder factor
+   [g] = (3 - [<m^4>] / [<m^2>]^2) / 2 (a disorder-level average, as printed).  Host only. */
+int rfim_disorder_average(const double *thermals, int32_t n, int32_t R, double *out);
 
 /* State access for tests and checkpoint/resume.  spins: host int8[R][L^3] values +-1 in natural
    site order, indexed by replica r; t2r: int32[R] replica at temperature k; E: double[R] energy of

@@ -264,9 +264,13 @@ class Oracle:
 # ---- derived observables of Sec. 7 --------------------------------------------------------------
 # Readings: C = (N / T^2)(<e^2> - <e>^2) with e the energy per site (the printed L^3 prefactor);
 # xi = sqrt(N <m^2> / <F> - 1): the printed <M^2> taken as the zero-wave-number structure factor
-# (1/N) <(sum_i s_i)^2> = N <m^2>, which has F's normalisation; no 1/(2 sin(K/2)) factor, as printed.
+# (1/N) <(sum_i s_i)^2> = N <m^2>, which has F's normalisation; no 1/(2 sin(K/2)) factor, as printed;
+# +inf when <F> vanishes (a uniform lattice at every measurement).
 
 THERMAL_COLUMNS = ("e", "C", "absm", "m2", "m4", "F", "xi")
+# Any lattice with a spin against the others has F >= 4/N per measurement; averages below this
+# bound are rounding noise of uniform lattices (about 1e-32 L^3).
+F_ZERO = 1e-20
 
 
 def thermal(obs, F, n_meas, N, T):
@@ -285,8 +289,11 @@ def thermal(obs, F, n_meas, N, T):
     if F is not None:
         Fa = np.asarray(F, dtype=np.float64) / float(n_meas)
         out[:, 5] = Fa
-        arg = float(N) * avg[:, 3] / Fa - 1.0
-        out[:, 6] = np.where(arg >= 0.0, np.sqrt(np.maximum(arg, 0.0)), np.nan)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            arg = float(N) * avg[:, 3] / Fa - 1.0
+            xi = np.where(arg >= 0.0, np.sqrt(np.maximum(arg, 0.0)), np.nan)
+        # <F> below F_ZERO is the rounding of an exactly uniform lattice: xi diverges
+        out[:, 6] = np.where(Fa < F_ZERO, np.inf, xi)
     return out
 
 

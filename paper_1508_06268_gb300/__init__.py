@@ -39,7 +39,7 @@ class Config(C.Structure):
 class Obs(C.Structure):
     _fields_ = [("R", C.c_int32), ("T", C.c_void_p), ("e", C.c_void_p), ("e2", C.c_void_p),
                 ("absm", C.c_void_p), ("m2", C.c_void_p), ("m4", C.c_void_p), ("att", C.c_void_p),
-                ("acc", C.c_void_p), ("n_meas", C.c_int64)]
+                ("acc", C.c_void_p), ("n_meas", C.c_int64), ("F", C.c_void_p)]
 
 
 class ExchangeBuffers(C.Structure):
@@ -102,6 +102,9 @@ def load():
             L.rfim_exchange_noalloc.argtypes = [C.POINTER(ExchangeBuffers), u32, i64, P]
             L.rfim_selftest_grid.argtypes = [i32, i32, i32]
             L.rfim_selftest_wait.argtypes = [i32, i32]
+            L.rfim_set_measure_xi.argtypes = [P, i32]
+            L.rfim_thermal.argtypes = [C.POINTER(Obs), i32, P]
+            L.rfim_disorder_average.argtypes = [P, i32, i32, P]
             L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
@@ -110,7 +113,8 @@ def load():
                          "rfim_get_field", "rfim_selftest_bits", "rfim_profile",
                          "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
                          "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
-                         "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid", "rfim_selftest_wait"):
+                         "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid", "rfim_selftest_wait",
+                         "rfim_set_measure_xi", "rfim_thermal", "rfim_disorder_average"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -151,6 +155,39 @@ def selftest_grid(L: int, R: int, P: int) -> int:
 
 def selftest_bits(L: int, seed: int = 1) -> int:
     return load().rfim_selftest_bits(L, seed)
+
+
+THERMAL_COLUMNS = ("e", "C", "absm", "m2", "m4", "F", "xi")
+DISORDER_COLUMNS = ("e", "C", "absm", "xi", "g")
+
+
+def thermal(obs: dict, N: int) -> np.ndarray:
+    """rfim_thermal on an observables dict (Realization.observables or a served result)."""
+    R = len(obs["T"])
+    o = Obs()
+    keep = {k: np.ascontiguousarray(obs[k], dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4")}
+    for k, a in keep.items():
+        setattr(o, k, a.ctypes.data)
+    F = obs.get("F")
+    Fa = np.ascontiguousarray(F, dtype=np.float64) if F is not None else None
+    o.F = Fa.ctypes.data if Fa is not None else None
+    o.R, o.n_meas = R, int(obs["n_meas"])
+    out = np.zeros((R, 7), dtype=np.float64)
+    rc = load().rfim_thermal(C.byref(o), N, out.ctypes.data)
+    if rc != OK:
+        raise RfimError(rc, "rfim_thermal")
+    return out
+
+
+def disorder_average(thermals) -> np.ndarray:
+    """rfim_disorder_average over per-realization thermal arrays sharing one temperature set."""
+    t = np.ascontiguousarray(np.stack([np.asarray(a, dtype=np.float64) for a in thermals]))
+    n, R = t.shape[0], t.shape[1]
+    out = np.zeros((R, 5), dtype=np.float64)
+    rc = load().rfim_disorder_average(t.ctypes.data, n, R, out.ctypes.data)
+    if rc != OK:
+        raise RfimError(rc, "rfim_disorder_average")
+    return out
 
 
 def selftest_wait(spin_limit: int, set_flag: bool) -> int:
@@ -231,7 +268,7 @@ class Realization:
 
     def observables(self):
         R = self._R
-        arrs = {k: np.zeros(R, dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4")}
+        arrs = {k: np.zeros(R, dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4", "F")}
         att = np.zeros(max(R - 1, 1), dtype=np.uint64)
         acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
         o = Obs()
@@ -243,6 +280,14 @@ class Realization:
         arrs["n_meas"] = int(o.n_meas)
         arrs["sums"] = np.stack([arrs[k] for k in ("e", "e2", "absm", "m2", "m4")], axis=1)
         return arrs
+
+    def set_measure_xi(self, on=True):
+        """Enables the structure-factor measurement behind the correlation length (Sec. 7)."""
+        self._check(self._lib.rfim_set_measure_xi(self._h, 1 if on else 0))
+
+    def thermal(self):
+        """Per-temperature thermal averages [R][7] (THERMAL_COLUMNS) from the accumulators."""
+        return thermal(self.observables(), self.N)
 
     def get_state(self, spins=True, t2r=True, energies=False):
         R, N = self._R, self.N

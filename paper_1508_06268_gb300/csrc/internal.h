@@ -58,6 +58,9 @@ cudaError_t launch_field(const RealView &v, int32_t kind, uint32_t field_seed, f
                          float *hh_c, uint8_t *hbit_c, uint32_t *hbits, cudaStream_t st);
 cudaError_t launch_init_spins(const RealView &v, int32_t R, uint32_t stage, bool bitpack, cudaStream_t st);
 cudaError_t launch_exchange(const RealView &v, uint32_t j, int64_t measure_from, cudaStream_t st);
+// Adds each replica's structure factor F (Sec. 7 correlation length) to sumF[r2t[r]].
+cudaError_t launch_measure_xi(const RealView &v, const double *kcos, const double *ksin, double *sumF, bool bitpack,
+                              cudaStream_t st);
 cudaError_t launch_to_natural(const RealView &v, int32_t R, bool bitpack, int8_t *out, cudaStream_t st);
 cudaError_t launch_from_natural(const RealView &v, int32_t R, bool bitpack, const int8_t *in, cudaStream_t st);
 cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st);

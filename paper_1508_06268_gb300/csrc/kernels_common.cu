@@ -262,6 +262,43 @@ __global__ void k_energy_int8_rows(RealView v, double J, double h) {
   }
 }
 
+// Structure factor F of the correlation length (Sec. 7; the spins s_i read for the printed h_i)
+// of every replica, added to the accumulator of the replica's temperature after an exchange step:
+// F = (1 / 3N) sum over the axes d of |sum_i s_i e^{i K i_d}|^2, K = 2 pi / L.  One CTA per
+// replica: exact integer marginals S_d[t] = sum of the spins with coordinate t along axis d
+// (shared-memory atomics), then the Fourier sums in double in a fixed order from tables
+// cos(K t), sin(K t) computed on the host.
+__global__ void k_measure_xi(RealView v, const double *kcos, const double *ksin, double *sumF, bool bitpack) {
+  extern __shared__ int marg[];  // [3][L]
+  const int32_t r = blockIdx.x, L = v.L, Lh = v.Lh;
+  const int64_t half = (int64_t)v.N / 2;
+  for (int t = threadIdx.x; t < 3 * L; t += blockDim.x) marg[t] = 0;
+  __syncthreads();
+  for (int32_t c = 0; c < 2; ++c) {
+    for (int64_t q = threadIdx.x; q < half; q += blockDim.x) {
+      const int si = 2 * get_spin(v, bitpack, r, c, q) - 1;
+      const Site s = site_of_q(L, Lh, c, q);
+      atomicAdd(&marg[s.x], si);
+      atomicAdd(&marg[L + s.y], si);
+      atomicAdd(&marg[2 * L + s.z], si);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double F = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double cs = 0.0, sn = 0.0;
+      for (int t = 0; t < L; ++t) {
+        cs = __dadd_rn(cs, __dmul_rn(kcos[t], (double)marg[d * L + t]));
+        sn = __dadd_rn(sn, __dmul_rn(ksin[t], (double)marg[d * L + t]));
+      }
+      F = __dadd_rn(F, __dadd_rn(__dmul_rn(cs, cs), __dmul_rn(sn, sn)));
+    }
+    const int k = v.r2t[r];
+    sumF[k] = __dadd_rn(sumF[k], F / (3.0 * (double)v.N));
+  }
+}
+
 // One exchange step j plus measurement (exchange.cuh), one CTA.
 __global__ void k_exchange(RealView v, uint32_t j, int64_t measure_from) { exchange_and_measure(v, j, measure_from); }
 
@@ -333,6 +370,12 @@ cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, c
     }
   } else
     k_energy<<<v.R, 512, 0, st>>>(v, J, h, bitpack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure_xi(const RealView &v, const double *kcos, const double *ksin, double *sumF, bool bitpack,
+                              cudaStream_t st) {
+  k_measure_xi<<<v.R, 512, (size_t)3 * v.L * sizeof(int), st>>>(v, kcos, ksin, sumF, bitpack);
   return cudaGetLastError();
 }
 

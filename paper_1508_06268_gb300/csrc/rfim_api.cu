@@ -43,6 +43,9 @@ struct rfim_ctx {
   double *obs = nullptr;
   int64_t *n_meas = nullptr;
   int8_t *scratch8 = nullptr;  // int8[Rcap][N] staging for state conversion
+  // structure-factor measurement (correlation length, Sec. 7): off unless enabled
+  bool xi_on = false;
+  double *sumF = nullptr, *kcos = nullptr, *ksin = nullptr;
   BitsPlan plan;
   std::string err;
   // optional kernel timing: event pairs around sweep launches (kind 0) and energy+exchange (kind 1)
@@ -141,7 +144,8 @@ void free_events(rfim_ctx *c) {
 void free_all(rfim_ctx *c) {
   free_events(c);
   void *ptrs[] = {c->spins8, c->bits, c->hraw, c->hh_c, c->hbit_c, c->hbits, c->thr, c->gjn, c->b2, c->b2l,
-                  c->beta_d, c->t2r, c->r2t, c->E, c->M, c->att, c->acc, c->obs, c->n_meas, c->scratch8};
+                  c->beta_d, c->t2r, c->r2t, c->E, c->M, c->att, c->acc, c->obs, c->n_meas, c->scratch8,
+                  c->sumF, c->kcos, c->ksin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   free_bits_plan(c->plan);
@@ -179,6 +183,7 @@ int reset_state(rfim_ctx *c, uint32_t stage) {
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->att, 0, c->Rcap * 8, c->stream));
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->acc, 0, c->Rcap * 8, c->stream));
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->obs, 0, (size_t)c->Rcap * 5 * 8, c->stream));
+  if (c->sumF) CUDA_OR_FAIL(c, cudaMemsetAsync(c->sumF, 0, (size_t)c->Rcap * 8, c->stream));
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->n_meas, 0, 8, c->stream));
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->E, 0, c->Rcap * 8, c->stream));
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->M, 0, c->Rcap * 8, c->stream));
@@ -221,6 +226,14 @@ int do_sweeps(rfim_ctx *c, int64_t n) {
   return RFIM_OK;
 }
 
+// After exchange step j: the structure factor of every replica when that step measured.
+int measure_xi_after(rfim_ctx *c, int64_t j, int64_t measure_from) {
+  if (!c->xi_on || j < measure_from) return RFIM_OK;
+  CUDA_OR_FAIL(c, launch_measure_xi(view_of(c), c->kcos, c->ksin, c->sumF, c->layout == RFIM_LAYOUT_BITPACK, c->stream));
+  c->launches += 1;
+  return RFIM_OK;
+}
+
 // Bit layout: n sweeps and the exchange step in one launch (fused tail).
 int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from) {
   RealView v = view_of(c);
@@ -232,7 +245,7 @@ int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from) {
   c->launches += 1;
   c->sweep += n;
   c->xstep += 1;
-  return RFIM_OK;
+  return measure_xi_after(c, c->xstep - 1, measure_from);
 }
 
 int do_exchange(rfim_ctx *c, int64_t measure_from) {
@@ -245,7 +258,7 @@ int do_exchange(rfim_ctx *c, int64_t measure_from) {
   CUDA_OR_FAIL(c, prof_end(c, stop));
   c->launches += 2;
   c->xstep += 1;
-  return RFIM_OK;
+  return measure_xi_after(c, c->xstep - 1, measure_from);
 }
 
 int do_run(rfim_ctx *c, int64_t n_sweeps, int32_t ex, int64_t measure_from) {
@@ -488,6 +501,91 @@ int rfim_observables(rfim_ctx *ctx, rfim_obs *out) {
   if (out->T) std::copy(c->T.begin(), c->T.end(), out->T);
   if (out->att) std::copy(att.begin(), att.begin() + (R - 1), out->att);
   if (out->acc) std::copy(acc.begin(), acc.begin() + (R - 1), out->acc);
+  if (out->F) {
+    if (c->sumF) {
+      CUDA_OR_FAIL(c, cudaMemcpyAsync(out->F, c->sumF, (size_t)R * 8, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    } else {
+      std::fill(out->F, out->F + R, 0.0);
+    }
+  }
+  return RFIM_OK;
+}
+
+int rfim_set_measure_xi(rfim_ctx *ctx, int32_t on) {
+  if (!ctx) return RFIM_EINVAL;
+  rfim_ctx *c = ctx;
+  if (!on) {
+    c->xi_on = false;
+    return RFIM_OK;
+  }
+  int64_t nm = 0;
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(&nm, c->n_meas, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  if (nm > 0 && !c->xi_on) return fail(c, RFIM_ESTATE, "enable the structure-factor measurement before the first measurement");
+  if (!c->sumF) {
+    int rc;
+    if ((rc = dalloc(c, &c->sumF, (size_t)c->Rcap))) return rc;
+    if ((rc = dalloc(c, &c->kcos, (size_t)c->L))) return rc;
+    if ((rc = dalloc(c, &c->ksin, (size_t)c->L))) return rc;
+    const double K = 2.0 * 3.14159265358979323846 / (double)c->L;
+    std::vector<double> kc(c->L), ks(c->L);
+    for (int32_t t = 0; t < c->L; ++t) {
+      kc[t] = std::cos(K * (double)t);
+      ks[t] = std::sin(K * (double)t);
+    }
+    CUDA_OR_FAIL(c, cudaMemcpy(c->kcos, kc.data(), c->L * 8, cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(c->ksin, ks.data(), c->L * 8, cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->sumF, 0, (size_t)c->Rcap * 8, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  }
+  c->xi_on = true;
+  return RFIM_OK;
+}
+
+int rfim_thermal(const rfim_obs *obs, int32_t N, double *out) {
+  if (!obs || !out || N < 1 || obs->R < 1 || !obs->T || !obs->e || !obs->e2 || !obs->absm || !obs->m2 || !obs->m4)
+    return RFIM_EINVAL;
+  const double nan = std::nan(""), n = (double)obs->n_meas;
+  for (int32_t k = 0; k < obs->R; ++k) {
+    double *o = out + (size_t)k * 7;
+    if (obs->n_meas <= 0) {
+      for (int q = 0; q < 7; ++q) o[q] = nan;
+      continue;
+    }
+    const double e = obs->e[k] / n, e2 = obs->e2[k] / n, T = obs->T[k];
+    o[0] = e;
+    o[1] = (double)N / (T * T) * (e2 - e * e);
+    o[2] = obs->absm[k] / n;
+    o[3] = obs->m2[k] / n;
+    o[4] = obs->m4[k] / n;
+    if (obs->F) {
+      // <F> below 1e-20 is the rounding of an exactly uniform lattice (a lattice with a spin
+      // against the others has F >= 4/N per measurement): xi diverges
+      const double F = obs->F[k] / n, arg = (double)N * o[3] / F - 1.0;
+      o[5] = F;
+      o[6] = F < 1e-20 ? HUGE_VAL : (arg >= 0.0 ? std::sqrt(arg) : nan);
+    } else {
+      o[5] = o[6] = nan;
+    }
+  }
+  return RFIM_OK;
+}
+
+int rfim_disorder_average(const double *thermals, int32_t n, int32_t R, double *out) {
+  if (!thermals || !out || n < 1 || R < 1) return RFIM_EINVAL;
+  for (int32_t k = 0; k < R; ++k) {
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int32_t i = 0; i < n; ++i)
+      for (int q = 0; q < 7; ++q) s[q] += thermals[((size_t)i * R + k) * 7 + q];
+    for (int q = 0; q < 7; ++q) s[q] /= (double)n;
+    double *o = out + (size_t)k * 5;
+    o[0] = s[0];
+    o[1] = s[1];
+    o[2] = s[2];
+    o[3] = s[6];
+    o[4] = 0.5 * (3.0 - s[4] / (s[3] * s[3]));
+  }
   return RFIM_OK;
 }
 

@@ -565,6 +565,7 @@ int rfim_server_poll(rfim_server *s, uint64_t ticket, rfim_obs *out, double *lat
     if (out->T) std::copy(r.T.begin(), r.T.end(), out->T);
     if (out->att) std::copy(r.att.begin(), r.att.begin() + (r.R - 1), out->att);
     if (out->acc) std::copy(r.acc.begin(), r.acc.begin() + (r.R - 1), out->acc);
+    if (out->F) std::fill(out->F, out->F + r.R, 0.0);  // not measured in served runs
   }
   if (latency_s) *latency_s = r.latency_s;
   s->done.erase(it);

@@ -57,3 +57,30 @@ def test_create_without_gpu_fails_loudly():
 def test_grid_partition(L, R, P):
     import paper_1508_06268_gb300 as rf
     assert rf.selftest_grid(L, R, P) == 0
+
+
+def test_thermal_and_disorder_average_match_the_oracle():
+    """Host-side derived observables of Sec. 7 (rfim_thermal, rfim_disorder_average) against the
+    oracle's formulas on random accumulator sums."""
+    import numpy as np
+    import oracle
+    import paper_1508_06268_gb300 as rf
+    rng = np.random.default_rng(5)
+    R, N, n = 6, 512, 250
+    T = np.linspace(1.0, 4.0, R)
+    thermals_lib, thermals_orc = [], []
+    for _ in range(3):
+        e = rng.normal(-1.5, 0.05, size=(n, R))
+        m = rng.normal(0.3, 0.1, size=(n, R))
+        F = rng.uniform(0.5, 3.0, size=(n, R))
+        sums = np.stack([e.sum(0), (e * e).sum(0), np.abs(m).sum(0), (m * m).sum(0), (m ** 4).sum(0)], axis=1)
+        obs = {"T": T, "e": sums[:, 0], "e2": sums[:, 1], "absm": sums[:, 2], "m2": sums[:, 3], "m4": sums[:, 4],
+               "F": F.sum(0), "n_meas": n}
+        thermals_lib.append(rf.thermal(obs, N))
+        thermals_orc.append(oracle.thermal(sums, F.sum(0), n, N, T))
+        np.testing.assert_allclose(thermals_lib[-1], thermals_orc[-1], rtol=1e-12, equal_nan=True)
+    np.testing.assert_allclose(rf.disorder_average(thermals_lib), oracle.disorder_average(thermals_orc),
+                               rtol=1e-12, equal_nan=True)
+    no_F = dict(obs)
+    no_F.pop("F")
+    assert np.isnan(rf.thermal(no_F, N)[:, 5:]).all()

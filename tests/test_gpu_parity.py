@@ -401,3 +401,51 @@ def test_bounded_wait_expires_and_context_stays_usable():
     g.run(10, 5, 0)
     o.run(10, 5, 0)
     assert_same_state(g, o, "after an expired wait")
+
+
+@pytest.mark.parametrize("L,R,layout", [(8, 6, BP), (16, 5, BP), (8, 6, I8), (64, 4, BP)])
+def test_structure_factor_sums_match_oracle(L, R, layout):
+    """Correlation-length measurement (Sec. 7): the per-temperature sums of the structure factor
+    F equal the oracle's (bimodal field, identical trajectories; the sums differ only in the order
+    of double additions), and the thermal averages and xi agree."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    g, o = make_pair(L, temps, kind=BIM, layout=layout, h=1.5, field_seed=4, seed=21)
+    g.set_measure_xi(True)
+    o.set_measure_xi(True)
+    g.run(40, 4, 2)
+    o.run(40, 4, 2)
+    assert_same_state(g, o, "with the structure-factor measurement")
+    obs = g.observables()
+    # uniform lattices give F at the rounding level (~1e-29): compare those absolutely
+    np.testing.assert_allclose(obs["F"], o.observables_F(), rtol=1e-11, atol=1e-20)
+    want = oracle.thermal(o.observables(), o.observables_F(), o.n_meas, L ** 3, o.temps())
+    np.testing.assert_allclose(g.thermal(), want, rtol=1e-10, atol=1e-20, equal_nan=True)
+
+
+def test_structure_factor_must_be_enabled_before_measuring():
+    g = rf.Realization(8, inputs.geometric_temps(1.0, 3.0, 4), field_kind=BIM, layout=BP)
+    g.run(8, 4, 0)
+    with pytest.raises(rf.RfimError) as ei:
+        g.set_measure_xi(True)
+    assert ei.value.code == rf.ESTATE
+    assert not g.observables()["F"].any()
+
+
+def test_disorder_average_over_served_realizations():
+    """[.] over served realizations (Sec. 7) equals the oracle's average over the same
+    realizations (bimodal: identical accumulators)."""
+    L, R, n_real = 8, 6, 4
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    with rf.Server(mem_budget_bytes=64 << 20, max_slots=8) as srv:
+        tickets = [srv.submit(L, temps, 40, 5, 4, field_kind=BIM, h=1.5, field_seed=10 + k, realization=k)
+                   for k in range(n_real)]
+        served = [srv.wait(t) for t in tickets]
+    th_gpu = [rf.thermal(r, L ** 3) for r in served]
+    th_orc = []
+    for k in range(n_real):
+        o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=10 + k, seed=42,
+                          realization=k)
+        o.run(40, 5, 4)
+        th_orc.append(oracle.thermal(o.observables(), None, o.n_meas, L ** 3, o.temps()))
+    np.testing.assert_allclose(rf.disorder_average(th_gpu), oracle.disorder_average(th_orc), rtol=1e-12,
+                               equal_nan=True)

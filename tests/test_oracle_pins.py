@@ -424,6 +424,9 @@ def test_structure_factor_of_uniform_and_staggered_lattices():
     stripes = np.where(np.cos(2 * np.pi * x / L) >= 0, 1, -1).astype(np.int8).reshape(-1)  # half-period slabs in x
     o.set_spins(np.stack([up, stripes]))
     assert abs(o.structure_F(0)) < 1e-20  # a full period of cos and sin sums to zero
+    xi = oracle.thermal(np.array([[0.0, 0.0, 1.0, 1.0, 1.0]]), np.array([o.structure_F(0)]), 1, L ** 3,
+                        np.array([1.0]))[0, 6]
+    assert xi == np.inf  # an ordered lattice: the second-moment length diverges
     # slabs along x: only the x axis contributes, |sum_x s(x) e^{iKx}|^2 L^4 / (3 L^3)
     sx = np.where(np.cos(2 * np.pi * np.arange(L) / L) >= 0, 1.0, -1.0)
     want = abs(np.sum(sx * np.exp(2j * np.pi * np.arange(L) / L))) ** 2 * L ** 4 / (3 * L ** 3)
