@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--sweeps", type=int, default=SWEEPS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="c4", choices=["c4", "serve"])
+    p.add_argument("--workload", default="c4", choices=["c4", "serve", "adapt"])
+    p.add_argument("--adapt-L", type=int, default=32)
     p.add_argument("--realizations", type=int, default=128)
     p.add_argument("--serve-sweeps", type=int, default=2000)
     p.add_argument("--int-rates", action="store_true")
@@ -265,6 +266,79 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# Sec. 4 and the comparison of adaptive and homogeneous temperature sets (Table 1, the exchange-rate
+# figure): per L, the trial runs and insertions the paper used, 2000 exchange steps of 10 sweeps per
+# run, and equally spaced (homogeneous) sparse and dense sets on [T_MIN, T_MAX].  The text does not
+# print the sparse and dense replica counts (they are in the figure labels), so they are chosen
+# here: the adaptive set starts from the sparse one, and the dense one has more replicas than the
+# adaptive set ends with.
+ADAPT_CASES = {32: {"trials": 10, "inserts": 2, "sparse": 40, "dense": 80},
+               64: {"trials": 32, "inserts": 3, "sparse": 64, "dense": 192}}
+
+
+def run_adapt(args):
+    """Adaptive vs sparse and dense homogeneous temperature sets on this GPU: wall time of the
+    production runs and of the adaptation trials, and the spread of the adjacent exchange rates."""
+    import torch
+    import paper_1508_06268_gb300 as rf
+    from paper_1508_06268_gb300 import inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    Lx = args.adapt_L
+    case = ADAPT_CASES[Lx]
+    n_real = max(1, args.realizations if args.realizations != 128 else 4)
+    steps, ex = 2000, EX
+    sweeps = steps * ex
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    def rates(g):
+        o = g.observables()
+        att = o["att"].astype(np.float64)
+        return np.where(att > 0, o["acc"] / np.maximum(att, 1), 0.0)
+
+    res = {k: {"s": 0.0, "rates": []} for k in ("sparse-sim", "dense-sim", "adapt-trials", "adapt-sim")}
+    Rs = {}
+    for k in range(n_real):
+        common = dict(field_kind=rf.FIELD_GAUSSIAN, h=H, field_seed=1 + k, realization=k, layout=rf.LAYOUT_BITPACK)
+        for name, Rn in (("sparse-sim", case["sparse"]), ("dense-sim", case["dense"])):
+            g = rf.Realization(Lx, inputs.linear_temps(T_MIN, T_MAX, Rn), **common)
+            _, dt = timed(lambda: g.run(sweeps, ex, steps // 2))
+            res[name]["s"] += dt
+            res[name]["rates"].append(rates(g))
+            Rs[name] = Rn
+            g.close()
+        cap = case["sparse"] + case["trials"] * case["inserts"]
+        g = rf.Realization(Lx, inputs.linear_temps(T_MIN, T_MAX, case["sparse"]), R_capacity=cap, **common)
+        _, dt = timed(lambda: g.adapt_temps(case["trials"], sweeps, ex, case["inserts"]))
+        res["adapt-trials"]["s"] += dt
+        _, dt = timed(lambda: g.run(sweeps, ex, steps // 2))
+        res["adapt-sim"]["s"] += dt
+        res["adapt-sim"]["rates"].append(rates(g))
+        Rs["adapt-sim"] = g.R
+        g.close()
+    line = {
+        "metric": "adaptive vs homogeneous temperature sets: wall seconds and adjacent exchange rates",
+        "workload": f"L={Lx} Gaussian h={H}, {n_real} realizations, {steps} exchange steps x {ex} sweeps per run, "
+                    f"adaptation {case['trials']} trials x {case['inserts']} insertions, T in [{T_MIN}, {T_MAX}]",
+        "replicas": {"sparse": case["sparse"], "dense": case["dense"], "adaptive_final": Rs["adapt-sim"]},
+        "seconds": {k: round(v["s"], 3) for k, v in res.items()},
+        "adapt_total_s": round(res["adapt-trials"]["s"] + res["adapt-sim"]["s"], 3),
+        "exchange_rates": {k: {"min": float(np.mean([r.min() for r in v["rates"]])),
+                               "mean": float(np.mean([r.mean() for r in v["rates"]])),
+                               "max": float(np.mean([r.max() for r in v["rates"]]))}
+                           for k, v in res.items() if v["rates"]},
+        "paper_table1_s_2xK40_100_realizations": {"32": [670.25, 1417.04, 41.84, 1167, 1209.49],
+                                                  "64": [10386.75, 26697.17, 1689.46, 19994.70, 21684.15]},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_int_rates():
     """Builds and runs the GB300 issue-rate microbenchmark (the roofline's peak basis) and the
     instruction-mix ceiling of Philox plus the acceptance tests."""
@@ -288,6 +362,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "adapt":
+        run_adapt(args)
         return
     import torch
     import paper_1508_06268_gb300 as rf

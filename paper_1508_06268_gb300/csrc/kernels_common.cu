@@ -299,6 +299,70 @@ __global__ void k_measure_xi(RealView v, const double *kcos, const double *ksin,
   }
 }
 
+// The same marginals at L = 64, where a row (y, z) of one colour holds 32 sites, in-word site i at
+// x = 2 i + ((colour + y + z) & 1) (bit layout: bit 8 (i & 3) + (i >> 2) of the row's word): a warp
+// takes 32 rows at a time; for each in-word site a ballot over the rows gives the up spins of
+// the two columns x = 2i and 2i + 1, counted by lane i; row and plane sums come from popcounts.
+// INT8: the int8 layout at L = 64 (a row of one colour is 32 bytes of 0/1, site i at byte i),
+// turned into the same 32-bit row words with in-word site i at bit i.
+template <bool INT8>
+__global__ void k_measure_xi_rows64(RealView v, const double *kcos, const double *ksin, double *sumF) {
+  constexpr int L = 64, W = L * L * L / 64;  // rows (words) per colour
+  __shared__ int marg[3 * L];
+  const int32_t r = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < 3 * L; t += blockDim.x) marg[t] = 0;
+  __syncthreads();
+  int ax0 = 0, ax1 = 0;  // column sums of x = 2 lane and 2 lane + 1
+  for (int blk = warp; blk < 2 * W / 32; blk += nwarps) {
+    const int c = blk / (W / 32), wq = (blk % (W / 32)) * 32 + lane;
+    uint32_t w = 0u;
+    if (INT8) {
+      const uint4 *row = reinterpret_cast<const uint4 *>(v.spins8 + ((int64_t)r * 2 + c) * (W * 32) + (int64_t)wq * 32);
+      const uint4 a = row[0], b = row[1];
+      const uint32_t q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        w |= ((q[t] & 1u) | ((q[t] >> 7) & 2u) | ((q[t] >> 14) & 4u) | ((q[t] >> 21) & 8u)) << (4 * t);
+    } else {
+      w = v.bits[((int64_t)r * 2 + c) * W + wq];
+    }
+    const int y = wq & (L - 1), z = wq / L;
+    const int rs = 2 * __popc(w) - 32;
+    atomicAdd(&marg[L + y], rs);
+    int zs = rs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
+    if (lane == 0) atomicAdd(&marg[2 * L + z], zs);  // the 32 rows share z
+    const uint32_t odd = __ballot_sync(0xffffffffu, ((c + y + z) & 1) != 0);
+    const int n_odd = __popc(odd), n_even = 32 - n_odd;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (w >> (INT8 ? i : 8 * (i & 3) + (i >> 2))) & 1u);
+      if (lane == i) {
+        ax0 += 2 * __popc(m & ~odd) - n_even;
+        ax1 += 2 * __popc(m & odd) - n_odd;
+      }
+    }
+  }
+  atomicAdd(&marg[2 * lane], ax0);
+  atomicAdd(&marg[2 * lane + 1], ax1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double F = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double cs = 0.0, sn = 0.0;
+      for (int t = 0; t < L; ++t) {
+        cs = __dadd_rn(cs, __dmul_rn(kcos[t], (double)marg[d * L + t]));
+        sn = __dadd_rn(sn, __dmul_rn(ksin[t], (double)marg[d * L + t]));
+      }
+      F = __dadd_rn(F, __dadd_rn(__dmul_rn(cs, cs), __dmul_rn(sn, sn)));
+    }
+    const int k = v.r2t[r];
+    sumF[k] = __dadd_rn(sumF[k], F / (3.0 * (double)v.N));
+  }
+}
+
 // One exchange step j plus measurement (exchange.cuh), one CTA.
 __global__ void k_exchange(RealView v, uint32_t j, int64_t measure_from) { exchange_and_measure(v, j, measure_from); }
 
@@ -375,7 +439,12 @@ cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, c
 
 cudaError_t launch_measure_xi(const RealView &v, const double *kcos, const double *ksin, double *sumF, bool bitpack,
                               cudaStream_t st) {
-  k_measure_xi<<<v.R, 512, (size_t)3 * v.L * sizeof(int), st>>>(v, kcos, ksin, sumF, bitpack);
+  if (v.L == 64 && bitpack)
+    k_measure_xi_rows64<false><<<v.R, 512, 0, st>>>(v, kcos, ksin, sumF);
+  else if (v.L == 64)
+    k_measure_xi_rows64<true><<<v.R, 512, 0, st>>>(v, kcos, ksin, sumF);
+  else
+    k_measure_xi<<<v.R, 512, (size_t)3 * v.L * sizeof(int), st>>>(v, kcos, ksin, sumF, bitpack);
   return cudaGetLastError();
 }
 

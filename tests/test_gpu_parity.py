@@ -403,7 +403,7 @@ def test_bounded_wait_expires_and_context_stays_usable():
     assert_same_state(g, o, "after an expired wait")
 
 
-@pytest.mark.parametrize("L,R,layout", [(8, 6, BP), (16, 5, BP), (8, 6, I8), (64, 4, BP)])
+@pytest.mark.parametrize("L,R,layout", [(8, 6, BP), (16, 5, BP), (8, 6, I8), (64, 4, BP), (64, 3, I8)])
 def test_structure_factor_sums_match_oracle(L, R, layout):
     """Correlation-length measurement (Sec. 7): the per-temperature sums of the structure factor
     F equal the oracle's (bimodal field, identical trajectories; the sums differ only in the order
