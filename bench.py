@@ -278,7 +278,8 @@ ADAPT_CASES = {32: {"trials": 10, "inserts": 2, "sparse": 40, "dense": 80},
 
 def run_adapt(args):
     """Adaptive vs sparse and dense homogeneous temperature sets on this GPU: wall time of the
-    production runs and of the adaptation trials, and the spread of the adjacent exchange rates."""
+    production runs of every realization and of the adaptation trials (run once, on realization 0,
+    the set then shared), and the spread of the adjacent exchange rates."""
     import torch
     import paper_1508_06268_gb300 as rf
     from paper_1508_06268_gb300 import inputs
@@ -302,30 +303,30 @@ def run_adapt(args):
         return np.where(att > 0, o["acc"] / np.maximum(att, 1), 0.0)
 
     res = {k: {"s": 0.0, "rates": []} for k in ("sparse-sim", "dense-sim", "adapt-trials", "adapt-sim")}
-    Rs = {}
+
+    def common(k):
+        return dict(field_kind=rf.FIELD_GAUSSIAN, h=H, field_seed=1 + k, realization=k, layout=rf.LAYOUT_BITPACK)
+
+    # the adaptation runs once (trials on realization 0); every realization then uses its set
+    cap = case["sparse"] + case["trials"] * case["inserts"]
+    g = rf.Realization(Lx, inputs.linear_temps(T_MIN, T_MAX, case["sparse"]), R_capacity=cap, **common(0))
+    adapted, dt = timed(lambda: g.adapt_temps(case["trials"], sweeps, ex, case["inserts"]))
+    res["adapt-trials"]["s"] = dt
+    g.close()
     for k in range(n_real):
-        common = dict(field_kind=rf.FIELD_GAUSSIAN, h=H, field_seed=1 + k, realization=k, layout=rf.LAYOUT_BITPACK)
-        for name, Rn in (("sparse-sim", case["sparse"]), ("dense-sim", case["dense"])):
-            g = rf.Realization(Lx, inputs.linear_temps(T_MIN, T_MAX, Rn), **common)
+        for name, temps in (("sparse-sim", inputs.linear_temps(T_MIN, T_MAX, case["sparse"])),
+                            ("dense-sim", inputs.linear_temps(T_MIN, T_MAX, case["dense"])),
+                            ("adapt-sim", adapted)):
+            g = rf.Realization(Lx, temps, **common(k))
             _, dt = timed(lambda: g.run(sweeps, ex, steps // 2))
             res[name]["s"] += dt
             res[name]["rates"].append(rates(g))
-            Rs[name] = Rn
             g.close()
-        cap = case["sparse"] + case["trials"] * case["inserts"]
-        g = rf.Realization(Lx, inputs.linear_temps(T_MIN, T_MAX, case["sparse"]), R_capacity=cap, **common)
-        _, dt = timed(lambda: g.adapt_temps(case["trials"], sweeps, ex, case["inserts"]))
-        res["adapt-trials"]["s"] += dt
-        _, dt = timed(lambda: g.run(sweeps, ex, steps // 2))
-        res["adapt-sim"]["s"] += dt
-        res["adapt-sim"]["rates"].append(rates(g))
-        Rs["adapt-sim"] = g.R
-        g.close()
     line = {
         "metric": "adaptive vs homogeneous temperature sets: wall seconds and adjacent exchange rates",
         "workload": f"L={Lx} Gaussian h={H}, {n_real} realizations, {steps} exchange steps x {ex} sweeps per run, "
                     f"adaptation {case['trials']} trials x {case['inserts']} insertions, T in [{T_MIN}, {T_MAX}]",
-        "replicas": {"sparse": case["sparse"], "dense": case["dense"], "adaptive_final": Rs["adapt-sim"]},
+        "replicas": {"sparse": case["sparse"], "dense": case["dense"], "adaptive_final": len(adapted)},
         "seconds": {k: round(v["s"], 3) for k, v in res.items()},
         "adapt_total_s": round(res["adapt-trials"]["s"] + res["adapt-sim"]["s"], 3),
         "exchange_rates": {k: {"min": float(np.mean([r.min() for r in v["rates"]])),

@@ -160,13 +160,34 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   cudaDeviceGetAttribute(&sms_dev, cudaDevAttrMultiProcessorCount, 0);
   if (L == 64) {
     // clusters of 4 z slabs x 4 replicas, unless they would leave more than a fifth of the SMs
-    // idle (e.g. R = 70 after adaptation: 72 CTAs); then the grid-wide plan covers every SM
+    // idle (e.g. R = 70 after adaptation: 72 CTAs) or need more clusters than fit at once (a
+    // second wave; 36 clusters of 4 at one CTA per SM on GB300); then the grid-wide plan
     const int cluster_ctas = 4 * ((Rcap + 3) / 4);
-    if (sms_dev > 0 && cluster_ctas < (4 * sms_dev) / 5) {
-      p.S = 0; p.G = 4; p.GT = 4; p.threads = 512;
-    } else {
-      p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
+    p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
+    bool grid = sms_dev > 0 && cluster_ctas < (4 * sms_dev) / 5;
+    if (!grid) {
+      KernelFn cf = kernel_for(L, 4, 4, 512, bimodal);
+      const size_t smem = (size_t)4 * 2 * words_per_cta(L, 4) * 4 + tab_bytes(4);
+      int maxc = 0;
+      if (cf && cudaFuncSetAttribute((const void *)cf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                    cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cluster_ctas);
+        cfg.blockDim = dim3(512u);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 4;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&maxc, (const void *)cf, &cfg) != cudaSuccess) maxc = 0;
+      }
+      cudaGetLastError();
+      grid = maxc > 0 && cluster_ctas > 4 * maxc;
     }
+    if (grid) p.S = 0;
   } else if (L == 32) {
     p.S = 2; p.G = 1; p.GT = 1; p.threads = 256;  // two z slabs per replica, one word per thread
   } else if (L == 16) {
