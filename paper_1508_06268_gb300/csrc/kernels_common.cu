@@ -427,10 +427,10 @@ cudaError_t launch_init_spins(const RealView &v, int32_t R, uint32_t stage, bool
 cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st) {
   if (!bitpack && v.L % 8 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
     switch (v.L) {
-      case 16: k_energy_int8_rows<16><<<v.R, 512, 0, st>>>(v, J, h); break;
-      case 32: k_energy_int8_rows<32><<<v.R, 512, 0, st>>>(v, J, h); break;
-      case 64: k_energy_int8_rows<64><<<v.R, 512, 0, st>>>(v, J, h); break;
-      default: k_energy_int8_rows<0><<<v.R, 512, 0, st>>>(v, J, h); break;
+      case 16: k_energy_int8_rows<16><<<v.R, 1024, 0, st>>>(v, J, h); break;
+      case 32: k_energy_int8_rows<32><<<v.R, 1024, 0, st>>>(v, J, h); break;
+      case 64: k_energy_int8_rows<64><<<v.R, 1024, 0, st>>>(v, J, h); break;
+      default: k_energy_int8_rows<0><<<v.R, 1024, 0, st>>>(v, J, h); break;
     }
   } else
     k_energy<<<v.R, 512, 0, st>>>(v, J, h, bitpack);

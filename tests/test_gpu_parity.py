@@ -81,6 +81,7 @@ def test_random_start_bit_exact(L, layout):
     (64, 6, BP, 6, 3),        # replica count not a multiple of the cluster's replicas
     (24, 7, I8, 12, 3),       # word-parallel int8 kernel: L/2 = 12 sites per row, R not a multiple of 4
     (64, 5, I8, 4, 2),
+    (128, 2, I8, 2, 1),       # largest lattice tested: edge length only known at run time
 ])
 def test_bimodal_trajectory_bit_exact(L, R, layout, sweeps, ex):
     temps = inputs.geometric_temps(1.0, 5.0, R)
