@@ -232,8 +232,8 @@ def run_serve(args):
     temps = {L: inputs.geometric_temps(T_MIN, T_MAX, R_) for L, R_ in SERVE_R.items()}
     work = sum(L ** 3 * R_ * sw for L, R_, _ in reqs)
 
-    def batched(arrivals):
-        srv = rf.Server(mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4)
+    def batched(arrivals, xi=False):
+        srv = rf.Server(mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4, measure_xi=xi)
         t0 = time.perf_counter()
         pend, lat, i = {}, [], 0
         while len(lat) < len(reqs):
@@ -271,6 +271,8 @@ def run_serve(args):
     # warm-up (module load, graph capture), then the closed-loop capacity of the batched server
     batched(np.zeros(len(reqs)))
     _, span_closed, _ = batched(np.zeros(len(reqs)))
+    # the same with the structure factor of the correlation length measured in the batched kernel
+    _, span_closed_xi, _ = batched(np.zeros(len(reqs)), xi=True)
     rate = 0.8 * len(reqs) / span_closed  # realizations / s offered to both servers
     arrivals = np.cumsum(gaps) / rate
     arrivals -= arrivals[0]
@@ -284,6 +286,7 @@ def run_serve(args):
         "batched": {"p50_s": float(np.percentile(lat_b, 50)), "p99_s": float(np.percentile(lat_b, 99)),
                     "attempts_per_ns": work / (span_b * 1e9), "makespan_s": span_b,
                     "closed_loop_attempts_per_ns": work / (span_closed * 1e9),
+                    "closed_loop_xi_attempts_per_ns": work / (span_closed_xi * 1e9),
                     "graph_launches": st["graph_launches"], "grid": st["grid"]},
         "per_realization": {"p50_s": float(np.percentile(lat_s, 50)), "p99_s": float(np.percentile(lat_s, 99)),
                             "attempts_per_ns": work / (span_s * 1e9), "makespan_s": span_s},

@@ -194,6 +194,8 @@ typedef struct {
   uint64_t mem_budget_bytes;    /* device arena for resident realizations (admission control) */
   int32_t max_slots;            /* realizations resident at the same time, >= 1 */
   int32_t intervals_per_launch; /* exchange intervals per graph replay, >= 1 */
+  int32_t measure_xi;           /* != 0: also accumulate the structure factor F (rfim_set_measure_xi)
+                                   on every measuring exchange step, fused into the batched kernel */
 } rfim_server_config;
 typedef struct {
   int64_t queued, resident, completed, graph_launches;
@@ -210,7 +212,8 @@ int rfim_server_submit(rfim_server *s, const rfim_config *cfg, int64_t n_sweeps,
                        int64_t measure_from, uint64_t *ticket);
 /* RFIM_EBUSY while queued or running; RFIM_OK once finished: fills out (caller-owned arrays sized
    for its R, any may be NULL) and *latency_s (seconds from submit to retirement), then forgets the
-   ticket.  RFIM_EINVAL for an unknown ticket; RFIM_ENOMEM if the realization cannot fit. */
+   ticket.  out->F is the structure-factor sum when the server measures it, else zeros.
+   RFIM_EINVAL for an unknown ticket; RFIM_ENOMEM if the realization cannot fit. */
 int rfim_server_poll(rfim_server *s, uint64_t ticket, rfim_obs *out, double *latency_s);
 int rfim_server_stats(rfim_server *s, rfim_server_info *out);
 /* Stops the worker (resident work is abandoned) and frees everything.  NULL is accepted. */

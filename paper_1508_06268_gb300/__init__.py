@@ -54,7 +54,7 @@ class ExchangeBuffers(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
-                ("intervals_per_launch", C.c_int32)]
+                ("intervals_per_launch", C.c_int32), ("measure_xi", C.c_int32)]
 
 
 class ServerInfo(C.Structure):
@@ -328,10 +328,10 @@ class Realization:
 class Server:
     """Continuous-batching server of independent realizations (include/rfim.h, serving section)."""
 
-    def __init__(self, mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4):
+    def __init__(self, mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4, measure_xi=False):
         self._lib = load()
         self._h = None
-        cfg = ServerConfig(mem_budget_bytes, max_slots, intervals_per_launch)
+        cfg = ServerConfig(mem_budget_bytes, max_slots, intervals_per_launch, 1 if measure_xi else 0)
         out = C.c_void_p()
         rc = self._lib.rfim_server_create(C.byref(cfg), C.byref(out))
         if rc != OK:
@@ -381,7 +381,7 @@ class Server:
     def poll(self, ticket):
         """None while queued or running; the observables dict (plus latency_s) once finished."""
         R = self._R.get(ticket, 2)
-        arrs = {k: np.zeros(R, dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4")}
+        arrs = {k: np.zeros(R, dtype=np.float64) for k in ("T", "e", "e2", "absm", "m2", "m4", "F")}
         att = np.zeros(max(R - 1, 1), dtype=np.uint64)
         acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
         o = Obs()

@@ -11,8 +11,11 @@ namespace rfim {
 // Exchange step j (Eq. 2 read as W = min(1, e^Delta), Delta = (beta_k - beta_k+1)(E_a - E_b))
 // over the disjoint pairs k = j mod 2, j mod 2 + 2, ... (odd xor even, Sec. 3.1 step 4),
 // swapping temperature indices through t2r / r2t (Sec. 3.3), then, if j >= measure_from, one
-// measurement per temperature of e = E/N, e^2, |m|, m^2, m^4 with m = M/N (Sec. 7).
-__device__ __forceinline__ void exchange_and_measure(const RealView &v, uint32_t j, int64_t measure_from) {
+// measurement per temperature of e = E/N, e^2, |m|, m^2, m^4 with m = M/N (Sec. 7).  With
+// sumF set, also adds the structure factor Fr[r] of the replica now at each temperature to sumF
+// (Fr written by other CTAs of this launch before their arrival, hence read through L2).
+__device__ __forceinline__ void exchange_and_measure(const RealView &v, uint32_t j, int64_t measure_from,
+                                                     const double *Fr = nullptr, double *sumF = nullptr) {
   const int32_t R = v.R;
   for (int32_t p = threadIdx.x;; p += blockDim.x) {
     const int32_t k = (int32_t)(j & 1u) + 2 * p;
@@ -46,6 +49,7 @@ __device__ __forceinline__ void exchange_and_measure(const RealView &v, uint32_t
       acc[2] = __dadd_rn(acc[2], fabs(m));
       acc[3] = __dadd_rn(acc[3], m2);
       acc[4] = __dadd_rn(acc[4], __dmul_rn(__dmul_rn(m2, m), m));
+      if (sumF) sumF[k] = __dadd_rn(sumF[k], __ldcg(Fr + a));
     }
     if (threadIdx.x == 0) *v.n_meas += 1;
   }

@@ -44,4 +44,12 @@ void temperature_tables(const double *T, int32_t R, float J, float h, uint32_t *
   for (int u = 0; u < 8; ++u) gjn[u] = J * (float)(2 * u - 6);
 }
 
+void wave_tables(int32_t L, double *kcos, double *ksin) {
+  const double K = 2.0 * 3.14159265358979323846 / (double)L;
+  for (int32_t t = 0; t < L; ++t) {
+    kcos[t] = std::cos(K * (double)t);
+    ksin[t] = std::sin(K * (double)t);
+  }
+}
+
 }  // namespace rfim

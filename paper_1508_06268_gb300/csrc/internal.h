@@ -52,6 +52,8 @@ int set_thread_error(int code, const std::string &msg);
 void bimodal_row(double beta, float J, float h, uint32_t out[32]);
 void temperature_tables(const double *T, int32_t R, float J, float h, uint32_t *thr, float *b2, float *b2l,
                         double *beta, float gjn[8]);
+// cos(K t), sin(K t) for t < L, K = 2 pi / L (the wave number of the Sec. 7 structure factor)
+void wave_tables(int32_t L, double *kcos, double *ksin);
 
 // kernels_common.cu
 cudaError_t launch_field(const RealView &v, int32_t kind, uint32_t field_seed, float h, float *hraw,

@@ -22,9 +22,9 @@ __device__ __forceinline__ void run_item(const SlotDesc &sd, const BatchItem &bi
   const uint32_t sweep0 = ctl->sweep0;
   const int nsw = ctl->nsw;
   if (sd.kind == kBimodal)
-    bits_interval<L, 1, GT, true>(sd.v, sd.G, bi.r0, bi.gact, 0, sweep0, nsw, sd.field4, xa);
+    bits_interval<L, 1, GT, true, true>(sd.v, sd.G, bi.r0, bi.gact, 0, sweep0, nsw, sd.field4, xa);
   else
-    bits_interval<L, 1, GT, false>(sd.v, sd.G, bi.r0, bi.gact, 0, sweep0, nsw, sd.field4, xa);
+    bits_interval<L, 1, GT, false, true>(sd.v, sd.G, bi.r0, bi.gact, 0, sweep0, nsw, sd.field4, xa);
 }
 
 __global__ void __launch_bounds__(kBatchThreads) k_batch_bits(const SlotDesc *__restrict__ slots, SlotCtl *ctls,

@@ -321,7 +321,7 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
                                bool exchange, uint32_t j, int64_t measure_from, double J, double h,
                                cudaStream_t st) {
-  ExchArgs xa;
+  ExchArgs xa{};
   xa.enabled = exchange ? 1 : 0;
   xa.j = j;
   xa.measure_from = measure_from;

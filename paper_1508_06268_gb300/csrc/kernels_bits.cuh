@@ -55,6 +55,10 @@ struct ExchArgs {
   unsigned int expected;
   SlotCtl *ctl;       // batched launches only (else null)
   unsigned int *err;  // error word: bit 0 = a bounded device wait expired
+  // structure factor of the correlation length (batched launches that measure it; else null):
+  // cos / sin(K t) tables [L], per-replica F of this interval [R], sums per temperature [R]
+  const double *kcos, *ksin;
+  double *Fr, *sumF;
 };
 
 __host__ __device__ __forceinline__ int64_t field4_index(int c, int64_t wq, int j, int64_t wpad) {
@@ -219,10 +223,99 @@ __device__ __forceinline__ T warp_reduce_sum(T x) {
   return x;
 }
 
+// Shared-memory marginals of the fused structure-factor measurement: 3 L ints per replica.
+constexpr int kXiMargInts = 768;
+__device__ __forceinline__ int *xi_marg_smem() {
+  __shared__ int m[kXiMargInts];
+  return m;
+}
+
+// Structure factor F of the correlation length (Sec. 7; the spins s_i read for the printed h_i)
+// of replicas [r0, r0 + gact), whole lattices in shared memory (one slab per replica):
+// F = (1 / 3N) sum over the axes d of |sum_t S_d[t] e^{i K t}|^2, K = 2 pi / L, from the exact
+// integer marginals S_d[t] (sum of the spins with coordinate t along axis d).  Word wq of colour
+// c holds sites q = 32 wq + i (in-word site i at bit 8 (i & 3) + (i >> 2)), i.e. RW = 32 / (L/2)
+// rows (y, z) of L/2 sites each, row rr at y = y0 + rr, x = 2 (i mod L/2) + ((c + y + z) & 1).
+// y and z marginals come from popcounts of rows and words; for x a warp takes 32 words and, per
+// in-word site i, ballots the spins and the row parities, counted by lane i.  The Fourier sums run
+// in double, one warp per replica with a fixed shuffle tree; F of replica r0 + g goes to xa.Fr.
+template <int L>
+__device__ __forceinline__ void xi_replicas(const uint32_t *sp, int r0, int gact, const ExchArgs &xa, int32_t N) {
+  constexpr int W = BitsGeom<L>::W, P = BitsGeom<L>::P, Lh = L / 2, RW = 32 / Lh, NB = (W + 31) / 32;
+  constexpr int CH = kXiMargInts / (3 * L);
+  constexpr uint32_t kRowMask = ((1u << (Lh / 4)) - 1u) * 0x01010101u;
+  static_assert(L >= 8 && L <= 64 && CH >= 1, "rows of one colour must tile a word");
+  int *marg = xi_marg_smem();
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int g0 = 0; g0 < gact; g0 += CH) {
+    const int ng = min(CH, gact - g0);
+    for (int t = tid; t < ng * 3 * L; t += nt) marg[t] = 0;
+    __syncthreads();
+    for (int u = wid; u < ng * 2 * NB; u += nw) {
+      const int gl = u / (2 * NB), c = (u / NB) & 1, wq = (u % NB) * 32 + lane;
+      const bool valid = wq < W;
+      const uint32_t w = valid ? sp[((size_t)(g0 + gl) * 2 + c) * W + wq] : 0u;
+      int *mg = marg + gl * 3 * L;
+      const int row0 = wq * RW, z = row0 / L, y0 = row0 % L;
+      if (valid) {
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) atomicAdd(&mg[L + y0 + rr], 2 * __popc(w & (kRowMask << (rr * (Lh / 4)))) - Lh);
+      }
+      if (P >= 32) {  // the warp's 32 words share one plane
+        int zs = 2 * __popc(w) - 32;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
+        if (lane == 0) atomicAdd(&mg[2 * L + z], zs);
+      } else if (valid) {
+        atomicAdd(&mg[2 * L + z], 2 * __popc(w) - 32);
+      }
+      const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+      const uint32_t odd0 = __ballot_sync(0xffffffffu, valid && ((c + y0 + z) & 1));
+      int ax0 = 0, ax1 = 0;  // columns x = 2 (lane mod L/2) and that + 1
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (w >> (8 * (i & 3) + (i >> 2))) & 1u);
+        if (lane == i) {
+          const uint32_t odd = ((i / Lh) & 1) ? (vmask & ~odd0) : odd0, even = vmask & ~odd;
+          ax0 = 2 * __popc(m & even) - __popc(even);
+          ax1 = 2 * __popc(m & odd) - __popc(odd);
+        }
+      }
+      atomicAdd(&mg[2 * (lane % Lh)], ax0);
+      atomicAdd(&mg[2 * (lane % Lh) + 1], ax1);
+    }
+    __syncthreads();
+    for (int gl = wid; gl < ng; gl += nw) {
+      const int *mg = marg + gl * 3 * L;
+      double F = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double cs = 0.0, sn = 0.0;
+        for (int t = lane; t < L; t += 32) {
+          cs = __dadd_rn(cs, __dmul_rn(xa.kcos[t], (double)mg[d * L + t]));
+          sn = __dadd_rn(sn, __dmul_rn(xa.ksin[t], (double)mg[d * L + t]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          cs = __dadd_rn(cs, __shfl_down_sync(0xffffffffu, cs, o));
+          sn = __dadd_rn(sn, __shfl_down_sync(0xffffffffu, sn, o));
+        }
+        F = __dadd_rn(F, __dadd_rn(__dmul_rn(cs, cs), __dmul_rn(sn, sn)));
+      }
+      if (lane == 0) {
+        xa.Fr[r0 + g0 + gl] = F / (3.0 * (double)N);
+        __threadfence();
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Fused exchange tail of an interval (Eq. 1 energies, then the last arrival takes exchange step
 // xa.j): slab partials of each replica from the lattice still in shared memory, an arrival count,
-// and for the last arrival the ordered reduction, E = -J B - F, exchange and measurement.
-template <int L, int S, bool BIM>
+// and for the last arrival the ordered reduction, E = -J B - F, exchange and measurement.  XI
+// (whole replicas, S = 1): on measuring steps with xa.sumF set, also the structure factor.
+template <int L, int S, bool BIM, bool XI = false>
 __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, int gact, int rank, int nsw,
                                               const float4 *__restrict__ field4, const ExchArgs &xa) {
   using Gm = BitsGeom<L>;
@@ -301,6 +394,9 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
     }
     __syncthreads();
   }
+  if constexpr (XI && S == 1) {
+    if (xa.sumF && (int64_t)xa.j >= xa.measure_from) xi_replicas<L>(sp, r0, gact, xa, v.N);
+  }
   sync_slabs<S>();  // peers may still read this CTA's halo planes
   if (tid == 0) {
     __threadfence();
@@ -325,7 +421,10 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
     v.M[r] = tm;
   }
   __syncthreads();
-  exchange_and_measure(v, xa.j, xa.measure_from);
+  if constexpr (XI && S == 1)
+    exchange_and_measure(v, xa.j, xa.measure_from, xa.Fr, xa.sumF);
+  else
+    exchange_and_measure(v, xa.j, xa.measure_from);
   if (tid == 0) {
     *xa.counter = 0u;
     if (xa.ctl) {
@@ -348,7 +447,7 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
 // One exchange interval of replicas [r0, r0 + gact) of realization v, slab `rank` of S: load into
 // shared memory, nsw sweeps, write back, and (xa.enabled) the energy partials and the exchange
 // tail.  All threads of the CTA call it; blockDim.x threads, dynamic shared memory >= the plan's.
-template <int L, int S, int GT, bool BIM>
+template <int L, int S, int GT, bool BIM, bool XI = false>
 __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, int gact, int rank, uint32_t sweep0,
                                               int nsw, const float4 *__restrict__ field4, const ExchArgs &xa) {
   using Gm = BitsGeom<L>;
@@ -439,7 +538,7 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl] = sp[t];
   }
-  if (xa.enabled) interval_tail<L, S, BIM>(v, G, r0, gact, rank, nsw, field4, xa);
+  if (xa.enabled) interval_tail<L, S, BIM, XI>(v, G, r0, gact, rank, nsw, field4, xa);
 }
 
 template <int L, int S, int GT, bool BIM, int NT>

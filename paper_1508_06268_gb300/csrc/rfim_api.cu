@@ -528,12 +528,8 @@ int rfim_set_measure_xi(rfim_ctx *ctx, int32_t on) {
     if ((rc = dalloc(c, &c->sumF, (size_t)c->Rcap))) return rc;
     if ((rc = dalloc(c, &c->kcos, (size_t)c->L))) return rc;
     if ((rc = dalloc(c, &c->ksin, (size_t)c->L))) return rc;
-    const double K = 2.0 * 3.14159265358979323846 / (double)c->L;
     std::vector<double> kc(c->L), ks(c->L);
-    for (int32_t t = 0; t < c->L; ++t) {
-      kc[t] = std::cos(K * (double)t);
-      ks[t] = std::sin(K * (double)t);
-    }
+    wave_tables(c->L, kc.data(), ks.data());
     CUDA_OR_FAIL(c, cudaMemcpy(c->kcos, kc.data(), c->L * 8, cudaMemcpyHostToDevice));
     CUDA_OR_FAIL(c, cudaMemcpy(c->ksin, ks.data(), c->L * 8, cudaMemcpyHostToDevice));
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->sumF, 0, (size_t)c->Rcap * 8, c->stream));

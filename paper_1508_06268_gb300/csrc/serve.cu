@@ -84,7 +84,7 @@ struct Result {
   int code = RFIM_OK;
   std::string msg;
   int32_t R = 0;
-  std::vector<double> T, obs;
+  std::vector<double> T, obs, F;
   std::vector<uint64_t> att, acc;
   int64_t n_meas = 0;
   double latency_s = 0.0, queued_s = 0.0;
@@ -155,6 +155,7 @@ struct rfim_server {
   int64_t graph_launches = 0, completed = 0, resident = 0;
   double busy_s = 0.0, attempts = 0.0;
   bool items_dirty = true;
+  bool measure_xi = false;
 };
 
 namespace {
@@ -175,7 +176,7 @@ int server_fail(rfim_server *s, int code, const std::string &msg) {
   return code;
 }
 
-size_t slot_bytes(int32_t L, int32_t R, int32_t kind) {
+size_t slot_bytes(int32_t L, int32_t R, int32_t kind, bool xi) {
   const size_t N = (size_t)L * L * L, W = N / 64, wpad = (W + 31) / 32 * 32;
   size_t b = 0;
   auto add = [&](size_t x) { b += Arena::round(x); };
@@ -187,6 +188,7 @@ size_t slot_bytes(int32_t L, int32_t R, int32_t kind) {
   add(R * 4); add(R * 4); add(R * 8); add(R * 8); add(R * 8); add(R * 8);  // t2r r2t E M att acc
   add((size_t)R * 40); add(8);                        // obs n_meas
   add(R * 8); add(R * 8); add(R * 8); add(R * 8); add(4);  // partials, counter
+  if (xi) { add(R * 8); add(R * 8); add(L * 8); add(L * 8); }  // Fr sumF kcos ksin
   return b;
 }
 
@@ -229,6 +231,15 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
   xa.partFi = (long long *)take(R * 8);
   xa.partF = (double *)take(R * 8);
   xa.counter = (unsigned int *)take(4);
+  double *kwave = nullptr;
+  if (s->measure_xi) {
+    xa.Fr = (double *)take(R * 8);
+    xa.sumF = (double *)take(R * 8);
+    kwave = (double *)take(L * 8);
+    double *ks = (double *)take(L * 8);
+    xa.kcos = kwave;
+    xa.ksin = ks;
+  }
   v.hh_c = hh_c; v.hbit_c = hbit_c; v.hbits = hbits; v.thr = thr; v.gjn = gjn; v.b2 = b2; v.b2l = b2l;
   v.beta_d = beta;
 
@@ -259,6 +270,8 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
   temperature_tables(rq.temps.data(), R, c.J, c.h, thr_h.data(), b2_h.data(), b2l_h.data(), beta_h.data(), gjn_h);
   std::vector<int32_t> id(R);
   std::iota(id.begin(), id.end(), 0);
+  std::vector<double> wave(2 * (size_t)L);
+  if (kwave) wave_tables(L, wave.data(), wave.data() + L);
   bool ok = ck(cudaMemcpyAsync(thr, thr_h.data(), thr_h.size() * 4, cudaMemcpyHostToDevice, st), "tables") &&
             ck(cudaMemcpyAsync(b2, b2_h.data(), R * 4, cudaMemcpyHostToDevice, st), "tables") &&
             ck(cudaMemcpyAsync(b2l, b2l_h.data(), R * 4, cudaMemcpyHostToDevice, st), "tables") &&
@@ -270,6 +283,9 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
             ck(cudaMemsetAsync(v.att, 0, R * 8, st), "zero") && ck(cudaMemsetAsync(v.acc, 0, R * 8, st), "zero") &&
             ck(cudaMemsetAsync(v.obs, 0, (size_t)R * 40, st), "zero") &&
             ck(cudaMemsetAsync(v.n_meas, 0, 8, st), "zero") && ck(cudaMemsetAsync(xa.counter, 0, 4, st), "zero") &&
+            (!kwave || (ck(cudaMemsetAsync(xa.sumF, 0, R * 8, st), "zero") &&
+                        ck(cudaMemcpyAsync(kwave, wave.data(), L * 8, cudaMemcpyHostToDevice, st), "tables") &&
+                        ck(cudaMemcpyAsync((void *)xa.ksin, wave.data() + L, L * 8, cudaMemcpyHostToDevice, st), "tables"))) &&
             ck(cudaStreamSynchronize(st), "slot init");
   if (!ok) return RFIM_ECUDA;
   const BatchShape sh = batch_shape(L);
@@ -305,6 +321,10 @@ void refresh(rfim_server *s) {
     copy_sync(s, res.att.data(), v.att, sl.R * 8, cudaMemcpyDeviceToHost);
     copy_sync(s, res.acc.data(), v.acc, sl.R * 8, cudaMemcpyDeviceToHost);
     copy_sync(s, &res.n_meas, v.n_meas, 8, cudaMemcpyDeviceToHost);
+    if (sl.desc.xa.sumF) {
+      res.F.resize(sl.R);
+      copy_sync(s, res.F.data(), sl.desc.xa.sumF, sl.R * 8, cudaMemcpyDeviceToHost);
+    }
     const Clock::time_point now = Clock::now();
     res.latency_s = seconds(sl.arrival, now);
     res.queued_s = seconds(sl.arrival, sl.admitted);
@@ -332,7 +352,7 @@ void refresh(rfim_server *s) {
         }
       if (free_slot < 0) break;
       const Request &front = s->pending.front();
-      const size_t need = slot_bytes(front.cfg.L, front.cfg.R, front.cfg.field_kind);
+      const size_t need = slot_bytes(front.cfg.L, front.cfg.R, front.cfg.field_kind, s->measure_xi);
       if (need > s->arena.size) {
         Result bad;
         bad.code = RFIM_ENOMEM;
@@ -464,6 +484,7 @@ int rfim_server_create(const rfim_server_config *cfg, rfim_server **out) {
   cudaGetDevice(&s->device);
   s->max_slots = cfg->max_slots;
   s->K = cfg->intervals_per_launch;
+  s->measure_xi = cfg->measure_xi != 0;
   s->slots.resize(s->max_slots);
   s->h_ctls.assign(s->max_slots, SlotCtl{});
   auto bail = [&](int code, const std::string &msg) {
@@ -565,7 +586,12 @@ int rfim_server_poll(rfim_server *s, uint64_t ticket, rfim_obs *out, double *lat
     if (out->T) std::copy(r.T.begin(), r.T.end(), out->T);
     if (out->att) std::copy(r.att.begin(), r.att.begin() + (r.R - 1), out->att);
     if (out->acc) std::copy(r.acc.begin(), r.acc.begin() + (r.R - 1), out->acc);
-    if (out->F) std::fill(out->F, out->F + r.R, 0.0);  // not measured in served runs
+    if (out->F) {
+      if (r.F.empty())
+        std::fill(out->F, out->F + r.R, 0.0);
+      else
+        std::copy(r.F.begin(), r.F.end(), out->F);
+    }
   }
   if (latency_s) *latency_s = r.latency_s;
   s->done.erase(it);

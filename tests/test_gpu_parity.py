@@ -433,11 +433,12 @@ def test_structure_factor_must_be_enabled_before_measuring():
 
 
 def test_disorder_average_over_served_realizations():
-    """[.] over served realizations (Sec. 7) equals the oracle's average over the same
-    realizations (bimodal: identical accumulators)."""
+    """[.] over served realizations (Sec. 7), the correlation length included, equals the oracle's
+    average over the same realizations (bimodal: identical accumulators; F sums up to the order of
+    the double additions)."""
     L, R, n_real = 8, 6, 4
     temps = inputs.geometric_temps(1.0, 5.0, R)
-    with rf.Server(mem_budget_bytes=64 << 20, max_slots=8) as srv:
+    with rf.Server(mem_budget_bytes=64 << 20, max_slots=8, measure_xi=True) as srv:
         tickets = [srv.submit(L, temps, 40, 5, 4, field_kind=BIM, h=1.5, field_seed=10 + k, realization=k)
                    for k in range(n_real)]
         served = [srv.wait(t) for t in tickets]
@@ -446,7 +447,8 @@ def test_disorder_average_over_served_realizations():
     for k in range(n_real):
         o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=10 + k, seed=42,
                           realization=k)
+        o.set_measure_xi(True)
         o.run(40, 5, 4)
-        th_orc.append(oracle.thermal(o.observables(), None, o.n_meas, L ** 3, o.temps()))
-    np.testing.assert_allclose(rf.disorder_average(th_gpu), oracle.disorder_average(th_orc), rtol=1e-12,
+        th_orc.append(oracle.thermal(o.observables(), o.observables_F(), o.n_meas, L ** 3, o.temps()))
+    np.testing.assert_allclose(rf.disorder_average(th_gpu), oracle.disorder_average(th_orc), rtol=1e-10,
                                equal_nan=True)

@@ -32,15 +32,51 @@ def submit(srv, L, R, kind, real, sweeps=SWEEPS):
 
 
 def test_results_same_alone_and_in_the_mix():
-    with rf.Server(mem_budget_bytes=256 << 20, max_slots=16, intervals_per_launch=2) as srv:
+    with rf.Server(mem_budget_bytes=256 << 20, max_slots=16, intervals_per_launch=2, measure_xi=True) as srv:
         tickets = [submit(srv, *m) for m in MIX]
         mixed = [srv.wait(t) for t in tickets]
     for m, res in zip(MIX, mixed):
-        with rf.Server(mem_budget_bytes=64 << 20, max_slots=1, intervals_per_launch=3) as solo:
+        with rf.Server(mem_budget_bytes=64 << 20, max_slots=1, intervals_per_launch=3, measure_xi=True) as solo:
             alone = solo.wait(submit(solo, *m))
         np.testing.assert_array_equal(res["sums"], alone["sums"], err_msg=str(m))
         np.testing.assert_array_equal(res["acc"], alone["acc"], err_msg=str(m))
+        np.testing.assert_array_equal(res["F"], alone["F"], err_msg=str(m))
         assert res["n_meas"] == alone["n_meas"] == SWEEPS // EX - 1
+
+
+@pytest.mark.parametrize("L,R,real", [(8, 18, 4), (16, 20, 1), (32, 9, 6), (64, 5, 7)])
+def test_served_structure_factor_equals_oracle(L, R, real):
+    """Structure factor of the correlation length (Sec. 7) measured inside the batched kernel,
+    replica groups with a ragged last group: the per-temperature sums of F equal the oracle's
+    (bimodal field, identical trajectories; only the order of the double additions differs)."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    with rf.Server(mem_budget_bytes=64 << 20, max_slots=2, measure_xi=True) as srv:
+        res = srv.wait(submit(srv, L, R, rf.FIELD_BIMODAL, real))
+    o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=10 + real, seed=42,
+                      realization=real)
+    o.set_measure_xi(True)
+    o.run(SWEEPS, EX, 1)
+    np.testing.assert_array_equal(res["sums"], o.observables())
+    assert res["F"].all()
+    np.testing.assert_allclose(res["F"], o.observables_F(), rtol=1e-11, atol=1e-20)
+
+
+def test_served_structure_factor_equals_single_realization_path():
+    """Gaussian field: the fused measurement of the batched kernel and the stand-alone kernel of a
+    single-realization run give the same F sums (same trajectory, both from integer marginals)."""
+    L, R = 32, 6
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    with rf.Server(mem_budget_bytes=64 << 20, max_slots=1, measure_xi=True) as srv:
+        res = srv.wait(srv.submit(L, temps, SWEEPS, EX, 1, field_kind=rf.FIELD_GAUSSIAN, field_seed=3, seed=42,
+                                  realization=2))
+    g = rf.Realization(L, temps, field_kind=rf.FIELD_GAUSSIAN, field_seed=3, seed=42, realization=2,
+                       layout=rf.LAYOUT_BITPACK)
+    g.set_measure_xi(True)
+    g.run(SWEEPS, EX, 1)
+    obs = g.observables()
+    # energies come from differently split error-free sums: equal up to the last bits
+    np.testing.assert_allclose(res["sums"], obs["sums"], rtol=1e-12)
+    np.testing.assert_allclose(res["F"], obs["F"], rtol=1e-12, atol=1e-20)
 
 
 @pytest.mark.parametrize("L,R,real", [(8, 5, 4), (16, 8, 1), (32, 9, 6), (64, 3, 7)])
@@ -52,6 +88,7 @@ def test_bimodal_served_equals_oracle(L, R, real):
                       realization=real)
     o.run(SWEEPS, EX, 1)
     np.testing.assert_array_equal(res["sums"], o.observables())
+    assert not res["F"].any()  # not measured unless the server is asked to
     att, acc = o.exchange_stats()
     np.testing.assert_array_equal(res["att"], att)
     np.testing.assert_array_equal(res["acc"], acc)
