@@ -85,6 +85,8 @@ def lib():
             L.orc_get_obs.argtypes = [P, P]
             L.orc_get_obsF.argtypes = [P, P]
             L.orc_set_measure_xi.argtypes = [P, i32]
+            L.orc_set_multihit.argtypes = [P, i32, i32]
+            L.orc_set_multihit.restype = i32
             L.orc_structure_F.argtypes = [P, i32]
             L.orc_structure_F.restype = f64
             L.orc_bimodal_threshold.argtypes = [f64, f64]
@@ -251,6 +253,12 @@ class Oracle:
 
     def set_measure_xi(self, on: bool):
         self._lib.orc_set_measure_xi(self._h, 1 if on else 0)
+
+    def set_multihit(self, mh: int, tile: int = 0):
+        """Multi-hit double 3D checkerboard (Sec. 3.2): mh local passes per tile visit, tiles of
+        edge `tile` (L divisible by 2 tile); mh = 0 restores the plain checkerboard."""
+        if self._lib.orc_set_multihit(self._h, mh, tile) != 0:
+            raise ValueError(f"invalid multi-hit setting mh={mh} tile={tile} for L={self.L}")
 
     def structure_F(self, r: int) -> float:
         return self._lib.orc_structure_F(self._h, r)

@@ -122,6 +122,7 @@ typedef struct {
   double *obs;     /* [Rcap][5] sums of e, e^2, |m|, m^2, m^4 per temperature index */
   double *obsF;    /* [Rcap] sums of the structure factor F per temperature index */
   int32_t measure_xi;
+  int32_t mh, tile; /* multi-hit double checkerboard: mh local passes per tile visit (0: off), tile edge */
   int64_t n_meas;
   int64_t sweep;   /* global sweep counter (0-based) */
   int64_t xstep;   /* global exchange step counter j (0-based) */
@@ -261,49 +262,83 @@ double orc_delta_e(const orc_t *o, int32_t r, int32_t x, int32_t y, int32_t z) {
   return (double)delta_e_float(o, r, x, y, z);
 }
 
-/* One checkerboard sweep (Eq. 3 colours; Sec. 3.1 step 4 Metropolis) of every replica. */
-void orc_sweep(orc_t *o) {
+/* Metropolis update (Sec. 3.1 step 4) of site (x,y,z) of replica r at temperature index k with
+   the random word `word`: accept iff dE <= 0 or the word passes the Boltzmann test, then flip. */
+static void metropolis_site(orc_t *o, int32_t r, int32_t k, int32_t x, int32_t y, int32_t z, uint32_t word) {
+  int64_t i = site_index(o->L, x, y, z);
+  int accept;
+  if (o->field_kind == ORC_FIELD_BIMODAL) {
+    int32_t si = o->s[(int64_t)r * o->N + i];
+    int32_t n = neighbour_sum(o, r, x, y, z);
+    int32_t sn = si * n;
+    int32_t sh = (si * (int32_t)o->hraw[i]) > 0 ? 1 : 0;
+    uint64_t thr = o->thr[(int64_t)k * 26 + (sn + 6) * 2 + sh];
+    accept = (uint64_t)word < thr;
+  } else {
+    float betaf = (float)(1.0 / o->T[k]);
+    float dE = delta_e_float(o, r, x, y, z);
+    float xarg = betaf * dE;
+    double u = (double)(word >> 8) * 0x1p-24;
+    accept = (dE <= 0.0f) || (u < exp(-(double)xarg));
+  }
+  if (accept) o->s[(int64_t)r * o->N + i] = (int8_t)(-o->s[(int64_t)r * o->N + i]);
+}
+
+/* One pass over the sites of colour `colour` (Eq. 3) of every replica, with the Philox counter
+   (q >> 2, r, c2, c3(METRO, stage, colour)), word q & 3, for the site q of the colour.  With
+   tile > 0 only the sites in tiles of coarse colour `coarse` are visited (double checkerboard). */
+static void colour_pass(orc_t *o, int32_t colour, uint32_t c2, int32_t tile, int32_t coarse) {
   int32_t L = o->L, Lh = L / 2;
   int64_t half = (int64_t)o->N / 2;
-  uint32_t sweep = (uint32_t)o->sweep;
   uint32_t w[4];
-  for (int32_t colour = 0; colour < 2; ++colour) {
-    for (int32_t r = 0; r < o->R; ++r) {
-      int32_t k = o->r2t[r];
-      double beta = 1.0 / o->T[k];
-      float betaf = (float)beta;
-      int64_t cached = -1;
-      for (int64_t q = 0; q < half; ++q) {
-        int32_t xh = (int32_t)(q % Lh);
-        int32_t y = (int32_t)((q / Lh) % L);
-        int32_t z = (int32_t)(q / ((int64_t)Lh * L));
-        int32_t x = 2 * xh + ((colour + y + z) & 1);
-        if ((q >> 2) != cached) {
-          orc_philox4x32_10(o->seed, o->realization, (uint32_t)(q >> 2), (uint32_t)r, sweep,
-                            tagword(ORC_TAG_METRO, o->stage, (uint32_t)colour), w);
-          cached = q >> 2;
-        }
-        uint32_t word = w[q & 3];
-        int64_t i = site_index(L, x, y, z);
-        int accept;
-        if (o->field_kind == ORC_FIELD_BIMODAL) {
-          int32_t si = o->s[(int64_t)r * o->N + i];
-          int32_t n = neighbour_sum(o, r, x, y, z);
-          int32_t sn = si * n;
-          int32_t sh = (si * (int32_t)o->hraw[i]) > 0 ? 1 : 0;
-          uint64_t thr = o->thr[(int64_t)k * 26 + (sn + 6) * 2 + sh];
-          accept = (uint64_t)word < thr;
-        } else {
-          float dE = delta_e_float(o, r, x, y, z);
-          float xarg = betaf * dE;
-          double u = (double)(word >> 8) * 0x1p-24;
-          accept = (dE <= 0.0f) || (u < exp(-(double)xarg));
-        }
-        if (accept) o->s[(int64_t)r * o->N + i] = (int8_t)(-o->s[(int64_t)r * o->N + i]);
+  for (int32_t r = 0; r < o->R; ++r) {
+    int32_t k = o->r2t[r];
+    int64_t cached = -1;
+    for (int64_t q = 0; q < half; ++q) {
+      int32_t xh = (int32_t)(q % Lh);
+      int32_t y = (int32_t)((q / Lh) % L);
+      int32_t z = (int32_t)(q / ((int64_t)Lh * L));
+      int32_t x = 2 * xh + ((colour + y + z) & 1);
+      if (tile > 0 && ((x / tile + y / tile + z / tile) & 1) != coarse) continue;
+      if ((q >> 2) != cached) {
+        orc_philox4x32_10(o->seed, o->realization, (uint32_t)(q >> 2), (uint32_t)r, c2,
+                          tagword(ORC_TAG_METRO, o->stage, (uint32_t)colour), w);
+        cached = q >> 2;
       }
+      metropolis_site(o, r, k, x, y, z, w[q & 3]);
     }
   }
+}
+
+/* One sweep of every replica.  Plain checkerboard (Eq. 3, Sec. 3.1 step 4): all colour-0 sites,
+   then all colour-1 sites, counter word 2 = the sweep.  Multi-hit double 3D checkerboard (Sec. 3.2;
+   the multi-hit runs of Sec. 6): the lattice is cut into tiles of tile^3 sites with coarse colour
+   (x/tile + y/tile + z/tile) mod 2; the tiles of coarse colour 0 are visited, then those of
+   coarse colour 1, and a visit makes mh local passes, each a black-white pass (fine colour 0,
+   then 1) over the visited tiles with the neighbouring tiles frozen.  Pass h of sweep s uses
+   counter word 2 = s * mh + h (mod 2^32), so every site draws a fresh word at each hit. */
+void orc_sweep(orc_t *o) {
+  uint32_t sweep = (uint32_t)o->sweep;
+  if (o->mh > 0) {
+    for (int32_t coarse = 0; coarse < 2; ++coarse)
+      for (int32_t h = 0; h < o->mh; ++h)
+        for (int32_t colour = 0; colour < 2; ++colour)
+          colour_pass(o, colour, sweep * (uint32_t)o->mh + (uint32_t)h, o->tile, coarse);
+  } else {
+    for (int32_t colour = 0; colour < 2; ++colour) colour_pass(o, colour, sweep, 0, 0);
+  }
   o->sweep += 1;
+}
+
+/* Selects the multi-hit double checkerboard (mh >= 1 local passes per tile visit, tiles of edge
+   tile with L divisible by 2 tile, so that the coarse colouring is periodic) or, with mh = 0,
+   the plain checkerboard.  Returns 0, or -1 for an invalid tile. */
+int32_t orc_set_multihit(orc_t *o, int32_t mh, int32_t tile) {
+  if (mh < 0) return -1;
+  if (mh > 0 && (tile < 1 || o->L % (2 * tile) != 0)) return -1;
+  o->mh = mh;
+  o->tile = mh > 0 ? tile : 0;
+  return 0;
 }
 
 /* Energy of replica r (Eq. 1): E = -J B - F with B summed over the 3N forward bonds. */

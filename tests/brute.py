@@ -71,3 +71,26 @@ def exact_energy_moments(L: int, J: float, hh: np.ndarray, beta: float):
     w = np.exp(-beta * (E - E.min()))
     w /= w.sum()
     return float(np.dot(w, E)), float(np.dot(w, E * E))
+
+
+def zero_temperature_multihit_sweep(spins: np.ndarray, L: int, J: float, hh: np.ndarray, tile: int,
+                                    mh: int) -> np.ndarray:
+    """One sweep of the multi-hit double 3D checkerboard at zero temperature (a flip is accepted
+    iff it does not raise the energy): tiles of tile^3 sites with coarse colour
+    (x//tile + y//tile + z//tile) mod 2, coarse colour 0 then 1; each visit makes mh black-white
+    passes over the visited tiles.  Each pass updates all its sites at once from numpy masks and
+    periodic shifts (its sites have no neighbour among themselves).  float32 energy change
+    2 s (J n + hh), as the model's float path rounds it."""
+    s = np.asarray(spins, dtype=np.int8).reshape(L, L, L).copy()  # [z][y][x]
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    fine = (x + y + z) % 2
+    coarse = (x // tile + y // tile + z // tile) % 2
+    h3 = np.asarray(hh, dtype=np.float32).reshape(L, L, L)
+    for c in (0, 1):
+        for _ in range(mh):
+            for f in (0, 1):
+                n = sum(np.roll(s, d, axis=a) for a in (0, 1, 2) for d in (1, -1)).astype(np.float32)
+                local = (np.float32(J) * n + h3).astype(np.float32)
+                flip = (fine == f) & (coarse == c) & (s.astype(np.float32) * local <= 0)
+                s[flip] = -s[flip]
+    return s.reshape(-1)

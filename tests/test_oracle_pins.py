@@ -5,7 +5,9 @@ Every test here runs on the CPU only.  Pins used: an independent Philox4x32-10 i
 enumeration of the 2x2x2 lattice (Boltzmann averages and the exact one-sweep transition matrix),
 closed forms (J = 0 independent spins, h = 0 low- and high-temperature expansions of the 3D
 Ising model), the exact stationary law of the exchange-only permutation chain, a sort-based
-reference for the min-heap selection of Sec. 4, and recomputation of the Sec. 7 accumulators.
+reference for the min-heap selection of Sec. 4, recomputation of the Sec. 7 accumulators, and
+for the multi-hit double checkerboard of Sec. 3.2 its reduction to the plain checkerboard, its
+flip count at infinite temperature and a numpy zero-temperature sweep.
 """
 from __future__ import annotations
 
@@ -497,3 +499,79 @@ def test_correlation_length_vanishes_for_independent_spins():
     assert F / n == pytest.approx(1.0, abs=0.15)
     xi = oracle.thermal(np.array([[0.0, 0.0, 0.0, m2, 0.0]]), np.array([F]), n, N, np.array([1.0]))[0, 6]
     assert np.isnan(xi) or xi < 0.5
+
+
+# ------------------------------------------------------------------ multi-hit double checkerboard
+@pytest.mark.parametrize("kind", [FIELD_BIMODAL, FIELD_GAUSSIAN])
+def test_multihit_single_site_tiles_single_pass_is_the_plain_checkerboard(kind):
+    """Tiles of one site and one pass per visit: the coarse colour of a tile is its site's colour,
+    so a sweep updates colour 0 then colour 1 with the plain counters (word 2 = sweep)."""
+    temps = inputs.geometric_temps(1.0, 5.0, 4)
+    a = Oracle(6, temps, h=1.5, field_kind=kind, field_seed=3, seed=11)
+    b = Oracle(6, temps, h=1.5, field_kind=kind, field_seed=3, seed=11)
+    a.set_multihit(1, 1)
+    a.run(12, 3, 1)
+    b.run(12, 3, 1)
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    np.testing.assert_array_equal(a.observables(), b.observables())
+
+
+@pytest.mark.parametrize("tile,mh", [(1, 3), (2, 1), (2, 2), (4, 3)])
+def test_multihit_every_site_flips_mh_times_at_infinite_temperature(tile, mh):
+    """beta -> 0 (T = 1e30): every attempt is accepted, so after n sweeps every spin has flipped
+    n mh times: s = s0 (-1)^(n mh).  Fails if a tile is visited twice or never, or a pass misses a
+    fine colour."""
+    o = Oracle(8, np.array([1e30, 2e30]), h=1.0, field_kind=FIELD_GAUSSIAN, field_seed=5, seed=2)
+    s0 = o.spins().astype(np.int64)
+    o.set_multihit(mh, tile)
+    for n in (1, 2, 3):
+        o.sweep(1)
+        np.testing.assert_array_equal(o.spins(), s0 * (-1) ** (n * mh))
+
+
+@pytest.mark.parametrize("tile,mh", [(2, 3), (4, 2), (1, 4)])
+def test_multihit_zero_temperature_matches_numpy_sweep(tile, mh):
+    """T -> 0 (T = 1e-30): a flip is accepted iff it does not raise the energy, so the dynamics is
+    deterministic; the oracle equals an independent numpy sweep in the tile / pass / colour order
+    of the double checkerboard."""
+    L = 8
+    o = Oracle(L, np.array([1e-30, 2e-30]), J=1.0, h=1.3, field_kind=FIELD_GAUSSIAN, field_seed=8, seed=4)
+    _, hh = o.field()
+    s = o.spins()
+    o.set_multihit(mh, tile)
+    changed_after_first_pass = False
+    for _ in range(3):
+        want = [brute.zero_temperature_multihit_sweep(s[r], L, 1.0, hh, tile, mh) for r in range(2)]
+        once = brute.zero_temperature_multihit_sweep(s[0], L, 1.0, hh, tile, 1)
+        changed_after_first_pass |= bool((once != want[0]).any())
+        o.sweep(1)
+        s = o.spins()
+        np.testing.assert_array_equal(s, np.stack(want))
+    if mh > 1 and tile > 1:
+        # the later passes change spins (with single-site tiles they cannot at zero temperature:
+        # the neighbours of a site stay frozen during its visit), so the order is tested
+        assert changed_after_first_pass
+
+
+def test_multihit_2x2x2_matches_exact_enumeration():
+    """Multi-hit sweeps keep the Boltzmann law: averages over a long chain with three hits per
+    visit equal the exact enumeration of the 2x2x2 lattice."""
+    L, J, h = 2, 1.0, 1.0
+    temps = np.array([1.0, 1.6, 2.6, 4.0])
+    o = Oracle(L, temps, J=J, h=h, field_kind=FIELD_BIMODAL, field_seed=6, seed=23)
+    o.set_multihit(3, 1)
+    _, hh = o.field()
+    o.run(200, 1, 10 ** 9)
+    mean, err = _binned(o, 20, 3000, 1)
+    for k, T in enumerate(temps):
+        exact = brute.exact_averages(L, J, hh, 1.0 / T)
+        for col in (0, 2, 3):
+            assert abs(mean[k, col] - exact[col]) < 5 * err[k, col] + 1e-12, (k, col)
+
+
+def test_multihit_rejects_tiles_that_do_not_tile_the_lattice():
+    o = Oracle(8, np.array([1.0, 2.0]))
+    for mh, tile in ((1, 3), (1, 8), (1, 0), (-1, 2)):
+        with pytest.raises(ValueError):
+            o.set_multihit(mh, tile)
+    o.set_multihit(0, 0)
