@@ -125,7 +125,8 @@ int rfim_adapt_temps(rfim_ctx *ctx, int32_t n_trials, int64_t sweeps_per_trial, 
 /* Observables: caller-owned host arrays sized for R (= the context's current R); any pointer may
    be NULL.  sums[k] are over the n_meas measurements at temperature index k (Sec. 7):
    e = E/N, e^2, |m|, m^2, m^4 with m = M/N, and F, the structure factor of the correlation length
-   (zeros unless rfim_set_measure_xi enabled it; always zeros in served results).  att/acc have
+   (zeros unless rfim_set_measure_xi enabled it; in served results zeros unless the server measures
+   it).  att/acc have
    R-1 entries (pair k, k+1).  Synchronous. */
 typedef struct {
   int32_t R;        /* out: current number of replicas */
@@ -145,6 +146,21 @@ int rfim_observables(rfim_ctx *ctx, rfim_obs *out);
    first measurement (RFIM_ESTATE otherwise); rfim_adapt_temps and restarts clear the sums with the
    other accumulators.  Synchronous. */
 int rfim_set_measure_xi(rfim_ctx *ctx, int32_t on);
+
+/* Multi-hit double 3D checkerboard (Sec. 3.2; the multi-hit runs of Sec. 6) for the following
+   sweeps, or (mh = 0) the plain checkerboard again.  The lattice is cut into tiles of tile^3
+   sites, coarse colour (x/tile + y/tile + z/tile) mod 2; one sweep visits the tiles of coarse
+   colour 0, then those of colour 1, and each visit makes mh black-white passes (fine colour 0,
+   then 1) over the visited tiles with the neighbouring tiles frozen: every site is attempted mh
+   times per sweep.  Pass h of sweep s draws the Philox words of counter
+   (q >> 2, r, s mh + h mod 2^32, c3(METRO, stage, fine colour)), so counters repeat after
+   2^32 / mh sweeps.  The paper keeps mh = 0 for its physics results; the multi-hit chain has the
+   same Boltzmann law but other dynamics.  Bit layout only; tile in {8, 16, 32}, L in {16, 32, 64}
+   divisible by 2 tile.  When the current launch shape has no multi-hit kernel (the grid-wide plan
+   of L = 64) the context switches to the default cluster shape of its L (synchronous in that
+   case).  Errors: RFIM_EINVAL (mh < 0, int8 layout, unsupported tile), RFIM_ENOMEM / RFIM_ECUDA
+   from the plan switch. */
+int rfim_set_multihit(rfim_ctx *ctx, int32_t mh, int32_t tile);
 
 /* Thermal averages of one realization (Sec. 7) from its accumulators (obs as filled by
    rfim_observables or rfim_server_poll; T, e, e2, absm, m2, m4 required, F optional), for a lattice

@@ -103,6 +103,7 @@ def load():
             L.rfim_selftest_grid.argtypes = [i32, i32, i32]
             L.rfim_selftest_wait.argtypes = [i32, i32]
             L.rfim_set_measure_xi.argtypes = [P, i32]
+            L.rfim_set_multihit.argtypes = [P, i32, i32]
             L.rfim_thermal.argtypes = [C.POINTER(Obs), i32, P]
             L.rfim_disorder_average.argtypes = [P, i32, i32, P]
             L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
@@ -114,7 +115,8 @@ def load():
                          "rfim_profile_read", "rfim_server_create", "rfim_server_submit",
                          "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
                          "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid", "rfim_selftest_wait",
-                         "rfim_set_measure_xi", "rfim_thermal", "rfim_disorder_average"):
+                         "rfim_set_measure_xi", "rfim_set_multihit", "rfim_thermal",
+                         "rfim_disorder_average"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -284,6 +286,11 @@ class Realization:
     def set_measure_xi(self, on=True):
         """Enables the structure-factor measurement behind the correlation length (Sec. 7)."""
         self._check(self._lib.rfim_set_measure_xi(self._h, 1 if on else 0))
+
+    def set_multihit(self, mh, tile=8):
+        """Multi-hit double 3D checkerboard (Sec. 3.2) for the following sweeps: mh black-white
+        passes per visit of the tiles of edge `tile`; mh = 0 restores the plain checkerboard."""
+        self._check(self._lib.rfim_set_multihit(self._h, mh, tile))
 
     def thermal(self):
         """Per-temperature thermal averages [R][7] (THERMAL_COLUMNS) from the accumulators."""

@@ -11,6 +11,7 @@
 #include "kernels_bits.cuh"
 #include "kernels_ws.cuh"
 #include "kernels_grid.cuh"
+#include "kernels_mh.cuh"
 #include "lattice.cuh"
 #include "sweep_bits.h"
 
@@ -54,6 +55,21 @@ KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
     if (L == 64 && S == 4) return bim ? (KernelFn)k_sweeps_ws<64, 4, true> : (KernelFn)k_sweeps_ws<64, 4, false>;
     if (L == 64 && S == 2) return bim ? (KernelFn)k_sweeps_ws<64, 2, true> : (KernelFn)k_sweeps_ws<64, 2, false>;
   }
+  return nullptr;
+}
+
+using MhFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *, ExchArgs, MultiHit);
+
+template <int L, int S, int GT, int NT>
+MhFn mh_pick(bool bim) {
+  return bim ? (MhFn)k_sweeps_bits_mh<L, S, GT, true, NT> : (MhFn)k_sweeps_bits_mh<L, S, GT, false, NT>;
+}
+
+// Multi-hit instances: the default cluster / single-CTA shapes of L = 64, 32, 16.
+MhFn mh_kernel_for(int L, int S, int GT, int NT, bool bim) {
+  if (L == 64 && S == 4 && GT == 4 && NT == 512) return mh_pick<64, 4, 4, 512>(bim);
+  if (L == 32 && S == 2 && GT == 1 && NT == 256) return mh_pick<32, 2, 1, 256>(bim);
+  if (L == 16 && S == 1 && GT == 1 && NT == 512) return mh_pick<16, 1, 1, 512>(bim);
   return nullptr;
 }
 
@@ -130,6 +146,30 @@ __global__ void k_build_field4(RealView v, float4 *field4, int64_t wpad) {
 }  // namespace
 
 bool bits_supported(int32_t L) { return L == 8 || L == 16 || L == 32 || L == 64; }
+
+bool multihit_tile_ok(int32_t L, int32_t tile) {
+  return (L == 16 || L == 32 || L == 64) && (tile == 8 || tile == 16 || tile == 32) && L % (2 * tile) == 0;
+}
+
+MultiHit make_multihit(int32_t L, int32_t mh, int32_t tile) {
+  MultiHit m;
+  if (mh <= 0 || !multihit_tile_ok(L, tile)) return m;
+  m.mh = mh;
+  m.tile = tile;
+  for (int j = 0; j < 8; ++j)
+    if ((((8 * j) % L) / tile) & 1) m.odd_tx |= 1u << j;
+  return m;
+}
+
+cudaError_t prepare_multihit(const BitsPlan &plan, bool bimodal) {
+  if (plan.S == 0) return cudaErrorInvalidConfiguration;
+  MhFn fn = mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, bimodal);
+  if (!fn) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+  if (e == cudaSuccess && plan.S > 1)
+    e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
 
 namespace {
 thread_local const char *t_plan_override = nullptr;
@@ -320,7 +360,7 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
 
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
                                bool exchange, uint32_t j, int64_t measure_from, double J, double h,
-                               cudaStream_t st) {
+                               cudaStream_t st, const MultiHit *mh) {
   ExchArgs xa{};
   xa.enabled = exchange ? 1 : 0;
   xa.j = j;
@@ -353,8 +393,11 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, gfn, v, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
   }
-  KernelFn fn = kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
-  if (!fn) return cudaErrorInvalidConfiguration;
+  const bool multihit = mh && mh->mh > 0;
+  if (multihit && plan.S == 0) return cudaErrorInvalidConfiguration;
+  KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
+  MhFn mfn = multihit ? mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal) : nullptr;
+  if (!fn && !mfn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(clusters * plan.S));
@@ -370,6 +413,8 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     cfg.attrs = at;
     cfg.numAttrs = 1;
   }
+  if (mfn)
+    return cudaLaunchKernelEx(&cfg, mfn, v, (int32_t)plan.G, sweep0, n_sweeps, (const float4 *)plan.field4, xa, *mh);
   return cudaLaunchKernelEx(&cfg, fn, v, (int32_t)plan.G, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
 }
 

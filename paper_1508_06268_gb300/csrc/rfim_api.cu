@@ -47,6 +47,7 @@ struct rfim_ctx {
   bool xi_on = false;
   double *sumF = nullptr, *kcos = nullptr, *ksin = nullptr;
   BitsPlan plan;
+  MultiHit mh;  // multi-hit double checkerboard (mh.mh == 0: plain checkerboard)
   std::string err;
   // optional kernel timing: event pairs around sweep launches (kind 0) and energy+exchange (kind 1)
   bool profiling = false;
@@ -210,7 +211,7 @@ int do_sweeps(rfim_ctx *c, int64_t n) {
   CUDA_OR_FAIL(c, prof_begin(c, 0, &stop));
   if (c->layout == RFIM_LAYOUT_BITPACK) {
     CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, false, 0u, 0, (double)c->J,
-                                       (double)c->h, c->stream));
+                                       (double)c->h, c->stream, &c->mh));
     c->launches += 1;
     c->sweep += n;
   } else {
@@ -240,7 +241,7 @@ int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from) {
   cudaEvent_t stop;
   CUDA_OR_FAIL(c, prof_begin(c, 0, &stop));
   CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, true, (uint32_t)c->xstep,
-                                     measure_from, (double)c->J, (double)c->h, c->stream));
+                                     measure_from, (double)c->J, (double)c->h, c->stream, &c->mh));
   CUDA_OR_FAIL(c, prof_end(c, stop));
   c->launches += 1;
   c->sweep += n;
@@ -536,6 +537,47 @@ int rfim_set_measure_xi(rfim_ctx *ctx, int32_t on) {
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
   }
   c->xi_on = true;
+  return RFIM_OK;
+}
+
+int rfim_set_multihit(rfim_ctx *ctx, int32_t mh, int32_t tile) {
+  if (!ctx) return RFIM_EINVAL;
+  rfim_ctx *c = ctx;
+  if (mh < 0) return fail(c, RFIM_EINVAL, "mh must be >= 0");
+  if (mh == 0) {
+    c->mh = MultiHit{};
+    return RFIM_OK;
+  }
+  if (c->layout != RFIM_LAYOUT_BITPACK) return fail(c, RFIM_EINVAL, "multi-hit sweeps need the bit layout");
+  if (!multihit_tile_ok(c->L, tile))
+    return fail(c, RFIM_EINVAL, "tile must be 8, 16 or 32 with L in {16, 32, 64} divisible by 2 tile (L=%d, tile=%d)",
+                c->L, tile);
+  const bool bim = c->kind == kBimodal;
+  if (prepare_multihit(c->plan, bim) != cudaSuccess) {
+    cudaGetLastError();
+    // the current launch shape has no multi-hit instance (e.g. the grid-wide plan): switch to the
+    // default cluster / single-CTA shape of this L
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    const char *shape = c->L == 64 ? "4,4,4,512" : c->L == 32 ? "2,1,1,256" : "1,8,1,512";
+    BitsPlan np;
+    set_plan_override(shape);
+    const int rc = make_bits_plan(c->L, c->Rcap, bim, &np, &c->err);
+    set_plan_override(nullptr);
+    if (rc) return rc;
+    if (np.field4) {
+      const cudaError_t e = build_field4(view_of(c), np, c->stream);
+      if (e != cudaSuccess) {
+        free_bits_plan(np);
+        return fail(c, RFIM_ECUDA, "field4 kernel: %s", cudaGetErrorString(e));
+      }
+      c->launches += 1;
+    }
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    free_bits_plan(c->plan);
+    c->plan = np;
+    CUDA_OR_FAIL(c, prepare_multihit(c->plan, bim));
+  }
+  c->mh = make_multihit(c->L, mh, tile);
   return RFIM_OK;
 }
 

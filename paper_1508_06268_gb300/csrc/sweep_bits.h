@@ -30,6 +30,21 @@ struct BitsPlan {
   int32_t sms = 0;
 };
 
+// Multi-hit double 3D checkerboard (Sec. 3.2, kernels_mh.cuh): mh local passes per tile visit
+// (0: the plain checkerboard), tiles of edge `tile` (a multiple of 8 dividing L / 2); odd_tx has
+// bit j set when Philox block j of a word (x in [8 j mod L, 8 j mod L + 8)) lies in a tile with
+// odd x index.
+struct MultiHit {
+  int32_t mh = 0, tile = 0;
+  uint32_t odd_tx = 0u;
+  int32_t pad = 0;
+};
+// Whether tiles of edge `tile` are supported at L; the setting for (L, mh, tile).
+bool multihit_tile_ok(int32_t L, int32_t tile);
+MultiHit make_multihit(int32_t L, int32_t mh, int32_t tile);
+// Whether the plan's shape has a multi-hit instance; sets its launch attributes.
+cudaError_t prepare_multihit(const BitsPlan &plan, bool bimodal);
+
 bool bits_supported(int32_t L);
 // Launch-shape tuner support: a thread-local candidate shape for the next make_bits_plan, the
 // remembered best shape per (L, R, field kind), and the candidates instantiated for each L.
@@ -42,8 +57,9 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st);
 void free_bits_plan(BitsPlan &plan);
 // n_sweeps sweeps; when exchange is true the launch ends with exchange step j (energies, swap
 // decisions, permutation, measurement when j >= measure_from).
+// With mh set (mh->mh > 0) the sweeps are multi-hit double-checkerboard sweeps.
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
                                bool exchange, uint32_t j, int64_t measure_from, double J, double h,
-                               cudaStream_t st);
+                               cudaStream_t st, const MultiHit *mh = nullptr);
 
 }  // namespace rfim

@@ -452,3 +452,69 @@ def test_disorder_average_over_served_realizations():
         th_orc.append(oracle.thermal(o.observables(), o.observables_F(), o.n_meas, L ** 3, o.temps()))
     np.testing.assert_allclose(rf.disorder_average(th_gpu), oracle.disorder_average(th_orc), rtol=1e-10,
                                equal_nan=True)
+
+
+# ------------------------------------------------------------------ multi-hit double checkerboard
+@pytest.mark.parametrize("L,R,tile,mh,sweeps,ex", [
+    (16, 5, 8, 3, 12, 3),
+    (32, 4, 8, 2, 8, 2),
+    (32, 3, 16, 1, 6, 3),
+    (64, 4, 8, 2, 4, 2),
+    (64, 6, 16, 3, 4, 2),     # two clusters, the second with a partial replica group
+    (64, 4, 32, 1, 4, 4),
+])
+def test_multihit_bimodal_trajectory_matches_oracle(L, R, tile, mh, sweeps, ex):
+    """Multi-hit double 3D checkerboard (Sec. 3.2): after plain sweeps, mh passes per tile visit
+    with fused exchange steps; spins, permutation and accumulators equal the oracle's.  At L = 64
+    and small R the context switches from the grid-wide plan to the cluster shape."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    g, o = make_pair(L, temps, kind=BIM, layout=BP, h=1.5, field_seed=7, seed=13)
+    g.run(2 * ex, ex, 0)
+    o.run(2 * ex, ex, 0)
+    g.set_multihit(mh, tile)
+    o.set_multihit(mh, tile)
+    g.run(sweeps, ex, 1)
+    o.run(sweeps, ex, 1)
+    assert_same_state(g, o, f"multi-hit mh={mh} tile={tile}")
+    np.testing.assert_array_equal(g.observables()["sums"], o.observables())
+    g.set_multihit(0)
+    o.set_multihit(0)
+    g.sweep(1)
+    o.sweep(1)
+    assert_same_state(g, o, "plain sweep after multi-hit")
+
+
+def test_multihit_gaussian_sweep_matches_oracle():
+    """Float field: one multi-hit sweep from the same state differs from the oracle only where a
+    decision on a rounding boundary (exp2 approximation against the oracle's double exp) flipped
+    and what it changed later in the sweep."""
+    L, R, tile, mh = 32, 4, 8, 2
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 5)
+    o = oracle.Oracle(L, temps, field_kind=EXP, field=field, seed=42)
+    o.run(3, 0, 0)
+    g = rf.Realization(L, temps, field_kind=EXP, field=field, seed=42, layout=BP)
+    g.set_state(spins=o.spins(), t2r=o.perm()[0], sweep=o.sweep_count, xstep=o.xstep_count)
+    g.set_multihit(mh, tile)
+    o.set_multihit(mh, tile)
+    before = o.spins()
+    g.sweep(1)
+    o.sweep(1)
+    a, b = g.get_state()["spins"], o.spins()
+    assert (b != before).mean() > 0.05  # the sweep did flip spins
+    assert (a != b).mean() <= 1e-4, int((a != b).sum())
+
+
+def test_multihit_settings_checked_at_the_boundary():
+    g = rf.Realization(64, inputs.geometric_temps(1.0, 5.0, 4), field_kind=BIM, layout=BP)
+    for mh, tile in ((-1, 8), (1, 24), (1, 64), (2, 4)):
+        with pytest.raises(rf.RfimError) as ei:
+            g.set_multihit(mh, tile)
+        assert ei.value.code == rf.EINVAL
+    g8 = rf.Realization(8, inputs.geometric_temps(1.0, 5.0, 4), field_kind=BIM, layout=BP)
+    with pytest.raises(rf.RfimError):
+        g8.set_multihit(1, 8)
+    gi = rf.Realization(16, inputs.geometric_temps(1.0, 5.0, 4), field_kind=BIM, layout=I8)
+    with pytest.raises(rf.RfimError):
+        gi.set_multihit(1, 8)
+    g.set_multihit(0)
