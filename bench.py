@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--sweeps", type=int, default=SWEEPS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="c4", choices=["c4", "serve", "adapt"])
+    p.add_argument("--workload", default="c4", choices=["c4", "serve", "adapt", "multihit"])
     p.add_argument("--adapt-L", type=int, default=32)
     p.add_argument("--realizations", type=int, default=128)
     p.add_argument("--serve-sweeps", type=int, default=2000)
@@ -368,6 +368,48 @@ def run_adapt(args):
     print(json.dumps(line), flush=True)
 
 
+def run_multihit(args):
+    """Multi-hit double 3D checkerboard (Sec. 3.2; the paper's mh = 100 spin-level runs) against the
+    plain checkerboard on the C4 shape: sweep-kernel time by CUDA events on the context's stream,
+    every attempt counted (mh per site and sweep)."""
+    import torch
+    import paper_1508_06268_gb300 as rf
+    from paper_1508_06268_gb300 import inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    L, R, attempts = 64, 128, 64 ** 3 * 128 * 400  # the work of 400 plain sweeps per measurement
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    rows = []
+    for kind, kname in ((rf.FIELD_GAUSSIAN, "gaussian"), (rf.FIELD_BIMODAL, "bimodal")):
+        for mh, tile in ((0, 0), (1, 8), (1, 32), (10, 8), (100, 8), (100, 16), (100, 32)):
+            sweeps = 400 // max(mh, 1)
+            ex = min(EX, sweeps)
+            g = rf.Realization(L, inputs.geometric_temps(T_MIN, T_MAX, R), field_kind=kind,
+                               layout=rf.LAYOUT_BITPACK)
+            if mh:
+                g.set_multihit(mh, tile)
+            g.run(max(ex, sweeps // 4), ex, 0)  # warm-up
+            g.profile(True)
+            g.run(sweeps, ex, 0)
+            p = g.profile_read()
+            g.profile(False)
+            g.close()
+            rows.append({"field": kname, "mh": mh, "tile": tile, "sweeps": sweeps,
+                         "attempts_per_ns": round(attempts / (p["sweep_ms"] * 1e6), 1)})
+    clk = clocks.stop()
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
+    for r in rows:
+        r["frac"] = round(r["attempts_per_ns"] / peak, 3)
+    line = {"metric": "spin-flip attempts/ns, multi-hit double checkerboard vs plain checkerboard",
+            "workload": f"C4 shape: L={L}, R={R} geometric [{T_MIN}, {T_MAX}], exchange every {EX} sweeps; "
+                        "mh black-white passes per tile visit, tiles of edge `tile` (mh = 0: plain)",
+            "rows": rows, "peak_attempts_per_ns": round(peak, 1),
+            "peak_basis": "Philox IMAD.WIDE limit at the sampled SM clock", "clocks": clk, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def run_int_rates():
     """Builds and runs the GB300 issue-rate microbenchmark (the roofline's peak basis) and the
     instruction-mix ceiling of Philox plus the acceptance tests."""
@@ -394,6 +436,9 @@ def main():
         return
     if args.workload == "adapt":
         run_adapt(args)
+        return
+    if args.workload == "multihit":
+        run_multihit(args)
         return
     import torch
     import paper_1508_06268_gb300 as rf
