@@ -4,7 +4,9 @@
 R=128), four exchange intervals of 10 sweeps.
 `python -m paper_1508_06268_gb300.microbench.prof_driver serve`: the batched serving kernel on a
 C5-shaped mix of 16 Gaussian realizations (L = 8, 16, 32, 64 with R = 16, 32, 64, 128), 400 sweeps
-each, submitted at once."""
+each, submitted at once.
+`python -m paper_1508_06268_gb300.microbench.prof_driver multihit`: the C4 shape with multi-hit
+double-checkerboard sweeps (mh = 100, tiles 8^3), four launches of one sweep each."""
 import sys
 
 import torch
@@ -22,6 +24,12 @@ if "serve" in sys.argv:
             srv.wait(t)
     torch.cuda.synchronize()
     print("ok", len(tickets))
+elif "multihit" in sys.argv:
+    g = rf.Realization(64, inputs.geometric_temps(1.0, 5.0, 128), field_kind=rf.FIELD_GAUSSIAN)
+    g.set_multihit(100, 8)
+    g.run(4, 1, 0)
+    torch.cuda.synchronize()
+    print("ok", g.get_state(spins=False)["sweep"])
 else:
     layout = rf.LAYOUT_INT8 if "int8" in sys.argv else rf.LAYOUT_BITPACK
     kind = rf.FIELD_BIMODAL if "bimodal" in sys.argv else rf.FIELD_GAUSSIAN
