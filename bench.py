@@ -38,7 +38,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweeps_bits<64,4,4,float,512> launch (one
 # exchange interval, 3.36e8 attempts) from an ncu capture of this kernel version; None when the
 # kernel changed since (profiles/k_sweeps_bits_L64_R128_gaussian.md).
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.327104e6, "k_halfsweep_int8_rows": None}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_halfsweep_int8_rows": None}
 
 
 def parse():

@@ -18,23 +18,21 @@ __device__ __forceinline__ float ex2_approx(float a) {
   return r;
 }
 
-// Continuous field (Gaussian or explicit).  f = J n + hh_i in float (J n tabulated exactly as the
-// float product): the same two roundings as the plain definition, so dE = 2 s f is the FP32 value
-// in that fixed order.  The table carries b = fl(-2 beta log2 e) signed by the spin, so
-// t = fl(b f) has exactly the sign of -dE and 2^t = exp(-beta dE) up to the roundings of b and of
-// the product.  The plain rule is: accept iff dE <= 0 or u < exp(-beta dE) with
-// u = (word >> 8) 2^-24.  Here it is evaluated as rz(word) < 2^t 2^32, where rz(word) is the word
-// rounded toward zero to a float (exactly 256 (word >> 8) for words >= 2^31, at most 128 above it
-// otherwise).  For dE <= 0, t >= 0 and ex2.approx(t) >= 1 (checked over every float in [0, 1) on
-// GB300), so the right side is >= 2^32 while rz(word) < 2^32: always accepted, as the rule says.
-// For dE > 0 the threshold differs from the double-precision one by a few 2^-23 relative
-// (ex2.approx and two float roundings), and a decision can differ only when u lands that close.
-__device__ __forceinline__ float boltzmann_exponent(float jn, float hh, float b) {
-  return __fmul_rn(b, __fadd_rn(jn, hh));
-}
+// Continuous field (Gaussian or explicit).  The table carries b = fl(-2 beta log2 e) signed by the
+// spin and bjn = fl(b J n); the exponent is t = fma(b, hh_i, bjn), one rounding of
+// b (J n + hh_i) = -beta dE log2 e, so 2^t = exp(-beta dE) up to the roundings of b, bjn and t.
+// The plain rule is: accept iff dE <= 0 or u < exp(-beta dE) with u = (word >> 8) 2^-24.  Here it
+// is evaluated as rz(word) < 2^t 2^32, where rz(word) is the word rounded toward zero to a float
+// (exactly 256 (word >> 8) for words >= 2^31, at most 128 above it otherwise).  t has the sign of
+// -dE except where J n + hh_i cancels to within a rounding of bjn (|J n + hh_i| below about
+// 2^-24 |J n|); for t >= 0, ex2.approx(t) >= 1 (checked over every float in [0, 1) on GB300), so
+// the right side is >= 2^32 while rz(word) < 2^32: accepted, as the rule says.  For dE > 0 the
+// threshold differs from the double-precision one by a few 2^-23 relative (ex2.approx and the
+// float roundings), and a decision can differ only when u lands that close.
+__device__ __forceinline__ float boltzmann_exponent(float bjn, float hh, float b) { return __fmaf_rn(b, hh, bjn); }
 
-__device__ __forceinline__ bool accept_float_l2e(uint32_t word, float jn, float hh, float b) {
-  const float p32 = __fmul_rn(ex2_approx(boltzmann_exponent(jn, hh, b)), 4294967296.0f);
+__device__ __forceinline__ bool accept_float_l2e(uint32_t word, float bjn, float hh, float b) {
+  const float p32 = __fmul_rn(ex2_approx(boltzmann_exponent(bjn, hh, b)), 4294967296.0f);
   return __uint2float_rz(word) < p32;
 }
 
@@ -42,8 +40,8 @@ __device__ __forceinline__ bool accept_float_l2e(uint32_t word, float jn, float 
 // forms rz(word) - 2^t 2^32 with a single rounding; the product is exact (a power-of-two scaling)
 // so the result is the correctly rounded difference, negative exactly when rz(word) < p32 and
 // +0 when they are equal.
-__device__ __forceinline__ uint32_t accept_float_sign(uint32_t word, float jn, float hh, float b) {
-  return __float_as_uint(__fmaf_rn(ex2_approx(boltzmann_exponent(jn, hh, b)), -4294967296.0f, __uint2float_rz(word)));
+__device__ __forceinline__ uint32_t accept_float_sign(uint32_t word, float bjn, float hh, float b) {
+  return __float_as_uint(__fmaf_rn(ex2_approx(boltzmann_exponent(bjn, hh, b)), -4294967296.0f, __uint2float_rz(word)));
 }
 
 }  // namespace rfim

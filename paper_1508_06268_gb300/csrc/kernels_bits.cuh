@@ -130,8 +130,8 @@ __device__ __forceinline__ uint32_t block_offsets(const PairSlices &p, int j) {
 
 // ---- per-replica decision tables in shared memory ------------------------------------------
 // A replica's table (bimodal: 32 thresholds - 1, indexed by up-count, spin, field bit; float
-// field: 16 pairs (J n, b), b = fl(-2 beta log2 e) signed by the spin, indexed by up-count and
-// spin) sits in its own 256-byte slot aligned to 256 bytes.  Byte k of a block's
+// field: 16 pairs (fl(b J n), b), b = fl(-2 beta log2 e) signed by the spin, indexed by up-count
+// and spin) sits in its own 256-byte slot aligned to 256 bytes.  Byte k of a block's
 // offset word then holds site k's byte offset within the slot, and one byte permute with the
 // slot address forms the entry address.
 constexpr uint32_t kTabSlot = 256;
@@ -158,7 +158,7 @@ __device__ __forceinline__ void tab_fill(const RealView &v, void *base, uint32_t
       reinterpret_cast<uint32_t *>(slot)[i] = v.thr[(int64_t)k * 32 + i];
     } else {
       const float b = (i >> 3) ? v.b2l[k] : -v.b2l[k];
-      reinterpret_cast<float2 *>(slot)[i] = make_float2(v.gjn[i & 7], b);
+      reinterpret_cast<float2 *>(slot)[i] = make_float2(__fmul_rn(b, v.gjn[i & 7]), b);
     }
   }
 }

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8(RealView v, int colour, 
         acc = accept_table(w.w[j], v.thr[(int64_t)k * 32 + idx]);
       } else {
         const float b2s = sbit ? v.b2l[k] : -v.b2l[k];
-        acc = accept_float_l2e(w.w[j], v.gjn[up], v.hh_c[colour * half + q], b2s);
+        acc = accept_float_l2e(w.w[j], __fmul_rn(b2s, v.gjn[up]), v.hh_c[colour * half + q], b2s);
       }
       if (acc) nxt ^= 1u << (8 * j);
     }
@@ -81,7 +81,7 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 template <bool kBimodalField, int GT, int LC>
 __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int colour, uint32_t sweep) {
   __shared__ __align__(256) uint32_t tab[64 * GT];  // per replica a 256-byte slot: bimodal 32 x (thr - 1),
-                                                    // float field 16 x (J n, +-b)
+                                                    // float field 16 x (b J n, +-b)
   const int32_t L = LC ? LC : v.L, Lh = L / 2;
   const int64_t half = (int64_t)L * L * Lh, plane = (int64_t)L * Lh;
   const int r0 = (int)blockIdx.y * GT;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
       tab[gg * 64 + i] = v.thr[(int64_t)k * 32 + i];
     } else if (i < 16) {
       const float b = (i >> 3) ? v.b2l[k] : -v.b2l[k];
-      reinterpret_cast<float2 *>(tab + gg * 64)[i] = make_float2(v.gjn[i & 7], b);
+      reinterpret_cast<float2 *>(tab + gg * 64)[i] = make_float2(__fmul_rn(b, v.gjn[i & 7]), b);
     }
   }
   __syncthreads();
