@@ -82,6 +82,7 @@ def test_random_start_bit_exact(L, layout):
     (24, 7, I8, 12, 3),       # word-parallel int8 kernel: L/2 = 12 sites per row, R not a multiple of 4
     (64, 5, I8, 4, 2),
     (128, 2, I8, 2, 1),       # largest lattice tested: edge length only known at run time
+    (64, 200, BP, 2, 1),      # more replicas than clusters of 4 fit at once: default grid-wide plan
 ])
 def test_bimodal_trajectory_bit_exact(L, R, layout, sweeps, ex):
     temps = inputs.geometric_temps(1.0, 5.0, R)
