@@ -38,7 +38,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweeps_bits<64,4,4,float,512> launch (one
 # exchange interval, 3.36e8 attempts) from an ncu capture of this kernel version; None when the
 # kernel changed since (profiles/k_sweeps_bits_L64_R128_gaussian.md).
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_halfsweep_int8_rows": None}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_halfsweep_int8_rows8": None}
 
 
 def parse():
@@ -503,7 +503,7 @@ def main():
                 "frac": achieved / peak,
                 "traffic": SWEEP_TRAFFIC_BYTES.get("k_sweeps_bits") if layout == rf.LAYOUT_BITPACK else None,
                 "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
-                "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8_rows",
+                "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8_rows8",
                 "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
                               f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
                               f"{sm_mhz:.0f} MHz (median sampled)",

@@ -20,7 +20,7 @@
 namespace rfim {
 
 #ifndef RFIM_INT8_GT
-#define RFIM_INT8_GT 4
+#define RFIM_INT8_GT 8
 #endif
 
 namespace {
@@ -74,17 +74,41 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   return d;
 }
 
-// grid: x over the groups of four sites, y over groups of GT replicas (GT temperature tables per
-// CTA); a thread takes one group of four sites in GT replicas, which share the field load.
-// LC: the edge length when fixed at compile time (index arithmetic by shifts, replica strides as
-// address offsets), 0 for any L divisible by 8.
-template <bool kBimodalField, int GT, int LC>
-__global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int colour, uint32_t sweep) {
-  __shared__ __align__(256) uint32_t tab[64 * GT];  // per replica a 256-byte slot: bimodal 32 x (thr - 1),
-                                                    // float field 16 x (b J n, +-b)
-  const int32_t L = LC ? LC : v.L, Lh = L / 2;
-  const int64_t half = (int64_t)L * L * Lh, plane = (int64_t)L * Lh;
-  const int r0 = (int)blockIdx.y * GT;
+// Decisions of the four sites of one Philox block: 0/1 spin bytes `cur`, up-count bytes `up`,
+// field bits `hb` (bimodal) or values `h4` (float), table slot `slot`.  Returns 0x01 in the byte
+// of every accepted site.
+template <bool kBimodalField>
+__device__ __forceinline__ uint32_t decide4(const Words4 &w, uint32_t cur, uint32_t up, uint32_t hb, const float4 &h4,
+                                            uint32_t slot) {
+  if (kBimodalField) {
+    const uint32_t offs = ((hb << 4) | (cur << 3) | up) << 2;  // per byte: table index x 4
+    uint32_t flips = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t t;
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(__byte_perm(offs, slot, 0x7650u | (uint32_t)j)));
+      if (accept_table(w.w[j], t)) flips |= 1u << (8 * j);
+    }
+    return flips;
+  }
+  const float hk[4] = {h4.x, h4.y, h4.z, h4.w};
+  const uint32_t offs = ((cur << 3) | up) << 3;  // per byte: table index x 8
+  uint32_t sg[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 e;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(e.x), "=f"(e.y) : "r"(__byte_perm(offs, slot, 0x7650u | (uint32_t)j)));
+    sg[j] = accept_float_sign(w.w[j], e.x, hk[j], e.y);
+  }
+  // byte j = 0xFF where site j is accepted (sign of the top byte of sg[j]), then one bit per byte
+  const uint32_t m01 = prmt(sg[0], sg[1], 0x00FBu), m23 = prmt(sg[2], sg[3], 0xFB00u);
+  return ((m01 & 0x0000FFFFu) | (m23 & 0xFFFF0000u)) & 0x01010101u;
+}
+
+// Per-replica decision tables of the CTA's GT replicas (64 words each: bimodal 32 x (thr - 1),
+// float field 16 x (b J n, +-b)), filled by all threads.
+template <bool kBimodalField, int GT>
+__device__ __forceinline__ void int8_tables(const RealView &v, uint32_t *tab, int r0) {
   for (int t = threadIdx.x; t < GT * 32; t += blockDim.x) {
     const int gg = t >> 5, i = t & 31, r = min(r0 + gg, v.R - 1), k = v.r2t[r];
     if (kBimodalField) {
@@ -94,6 +118,19 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
       reinterpret_cast<float2 *>(tab + gg * 64)[i] = make_float2(__fmul_rn(b, v.gjn[i & 7]), b);
     }
   }
+}
+
+// grid: x over the groups of four sites, y over groups of GT replicas (GT temperature tables per
+// CTA); a thread takes one group of four sites in GT replicas, which share the field load.
+// LC: the edge length when fixed at compile time (index arithmetic by shifts, replica strides as
+// address offsets), 0 for any L divisible by 8.
+template <bool kBimodalField, int GT, int LC>
+__global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int colour, uint32_t sweep) {
+  __shared__ __align__(256) uint32_t tab[64 * GT];  // per replica a 256-byte slot
+  const int32_t L = LC ? LC : v.L, Lh = L / 2;
+  const int64_t half = (int64_t)L * L * Lh, plane = (int64_t)L * Lh;
+  const int r0 = (int)blockIdx.y * GT;
+  int8_tables<kBimodalField, GT>(v, tab, r0);
   __syncthreads();
   const int32_t g = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (g >= half / 4) return;
@@ -131,37 +168,90 @@ __global__ void __launch_bounds__(256) k_halfsweep_int8_rows(RealView v, int col
     const uint32_t cur = ld_u32(self + q0);
     const uint32_t slot = slot0 + 256u * gg;
     const Words4 w = philox10(v.seed, v.realization, (uint32_t)g, (uint32_t)r, sweep, tag);
-    uint32_t flips;
-    if (kBimodalField) {
-      const uint32_t offs = ((hb << 4) | (cur << 3) | up) << 2;  // per byte: table index x 4
-      flips = 0u;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t t;
-        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(__byte_perm(offs, slot, 0x7650u | (uint32_t)j)));
-        if (accept_table(w.w[j], t)) flips |= 1u << (8 * j);
-      }
-    } else {
-      const float hk[4] = {h4.x, h4.y, h4.z, h4.w};
-      const uint32_t offs = ((cur << 3) | up) << 3;  // per byte: table index x 8
-      uint32_t sg[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float2 e;
-        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(e.x), "=f"(e.y) : "r"(__byte_perm(offs, slot, 0x7650u | (uint32_t)j)));
-        sg[j] = accept_float_sign(w.w[j], e.x, hk[j], e.y);
-      }
-      // byte j = 0xFF where site j is accepted (sign of the top byte of sg[j]), then one bit per byte
-      const uint32_t m01 = prmt(sg[0], sg[1], 0x00FBu), m23 = prmt(sg[2], sg[3], 0xFB00u);
-      flips = ((m01 & 0x0000FFFFu) | (m23 & 0xFFFF0000u)) & 0x01010101u;
-    }
+    const uint32_t flips = decide4<kBimodalField>(w, cur, up, hb, h4, slot);
     *reinterpret_cast<uint32_t *>(self + q0) = cur ^ flips;
+  }
+}
+
+__device__ __forceinline__ uint64_t ld_u64(const uint8_t *p) { return *reinterpret_cast<const uint64_t *>(p); }
+
+// The same with eight consecutive same-colour sites (two Philox blocks) per thread and replica,
+// for L % 16 == 0 (rows of L/2 sites hold whole groups of eight): each neighbour direction is one
+// 64-bit load, so a site costs half the loads and index arithmetic of the four-site kernel.
+template <bool kBimodalField, int GT, int LC>
+__global__ void __launch_bounds__(256) k_halfsweep_int8_rows8(RealView v, int colour, uint32_t sweep) {
+  __shared__ __align__(256) uint32_t tab[64 * GT];  // per replica a 256-byte slot
+  const int32_t L = LC ? LC : v.L, Lh = L / 2;
+  const int64_t half = (int64_t)L * L * Lh, plane = (int64_t)L * Lh;
+  const int r0 = (int)blockIdx.y * GT;
+  int8_tables<kBimodalField, GT>(v, tab, r0);
+  __syncthreads();
+  const int32_t g = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (g >= half / 8) return;
+  const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(tab);
+  const int32_t q0 = 8 * g;
+  const int32_t xh0 = q0 % Lh;
+  const int32_t row = q0 / Lh;
+  const int32_t y = row % L, z = row / L;
+  const bool odd = ((colour + y + z) & 1) != 0;
+  // x neighbours: the same eight bytes and the group after (odd rows) or before (even rows),
+  // periodic within the row, shifted by one byte; y, z: periodic rows and planes
+  const int32_t qa = (q0 - xh0) + (odd ? (xh0 + 8 == Lh ? 0 : xh0 + 8) : (xh0 == 0 ? Lh - 8 : xh0 - 8));
+  const int32_t yp = y == L - 1 ? q0 + Lh - (int32_t)plane : q0 + Lh;
+  const int32_t ym = y == 0 ? q0 - Lh + (int32_t)plane : q0 - Lh;
+  const int32_t zp = z == L - 1 ? q0 + (int32_t)plane - (int32_t)half : q0 + (int32_t)plane;
+  const int32_t zm = z == 0 ? q0 - (int32_t)plane + (int32_t)half : q0 - (int32_t)plane;
+  const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)colour);
+  float4 h4a = make_float4(0.f, 0.f, 0.f, 0.f), h4b = h4a;
+  uint64_t hb = 0u;
+  if (kBimodalField) {
+    hb = ld_u64(v.hbit_c + colour * half + q0);
+  } else {
+    const float4 *hp = reinterpret_cast<const float4 *>(v.hh_c + colour * half + q0);
+    h4a = __ldg(hp);
+    h4b = __ldg(hp + 1);
+  }
+  uint8_t *self0 = v.spins8 + ((int64_t)r0 * 2 + colour) * half;
+  const uint8_t *O0 = v.spins8 + ((int64_t)r0 * 2 + (colour ^ 1)) * half;
+#pragma unroll
+  for (int gg = 0; gg < GT; ++gg) {
+    const int r = r0 + gg;
+    if (r >= v.R) break;
+    uint8_t *self = self0 + 2 * half * gg;
+    const uint8_t *O = O0 + 2 * half * gg;
+    const uint64_t w0 = ld_u64(O + q0), wa = ld_u64(O + qa);
+    const uint64_t wx = odd ? ((w0 >> 8) | (wa << 56)) : ((w0 << 8) | (wa >> 56));
+    const uint64_t up = w0 + wx + ld_u64(O + yp) + ld_u64(O + ym) + ld_u64(O + zp) + ld_u64(O + zm);
+    const uint64_t cur = ld_u64(self + q0);
+    const uint32_t slot = slot0 + 256u * gg;
+    const Words4 wl = philox10(v.seed, v.realization, (uint32_t)(2 * g), (uint32_t)r, sweep, tag);
+    const Words4 wh = philox10(v.seed, v.realization, (uint32_t)(2 * g + 1), (uint32_t)r, sweep, tag);
+    const uint32_t flo = decide4<kBimodalField>(wl, (uint32_t)cur, (uint32_t)up, (uint32_t)hb, h4a, slot);
+    const uint32_t fhi = decide4<kBimodalField>(wh, (uint32_t)(cur >> 32), (uint32_t)(up >> 32),
+                                                (uint32_t)(hb >> 32), h4b, slot);
+    *reinterpret_cast<uint64_t *>(self + q0) = cur ^ ((uint64_t)fhi << 32 | flo);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_halfsweep_int8(const RealView &v, int colour, uint32_t sweep, cudaStream_t st) {
+  if (v.L % 16 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
+    constexpr int GT = RFIM_INT8_GT;
+    const int64_t groups = (int64_t)v.N / 16;
+    const dim3 grid((unsigned)((groups + 255) / 256), (unsigned)((v.R + GT - 1) / GT));
+    const bool bim = v.kind == kBimodal;
+    auto go = [&](auto kb, auto kf) {
+      (bim ? kb : kf)<<<grid, 256, 0, st>>>(v, colour, sweep);
+    };
+    switch (v.L) {
+      case 16: go(k_halfsweep_int8_rows8<true, GT, 16>, k_halfsweep_int8_rows8<false, GT, 16>); break;
+      case 32: go(k_halfsweep_int8_rows8<true, GT, 32>, k_halfsweep_int8_rows8<false, GT, 32>); break;
+      case 64: go(k_halfsweep_int8_rows8<true, GT, 64>, k_halfsweep_int8_rows8<false, GT, 64>); break;
+      default: go(k_halfsweep_int8_rows8<true, GT, 0>, k_halfsweep_int8_rows8<false, GT, 0>); break;
+    }
+    return cudaGetLastError();
+  }
   if (v.L % 8 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
     constexpr int GT = RFIM_INT8_GT;
     const int64_t groups = (int64_t)v.N / 8;
