@@ -65,7 +65,19 @@ cudaError_t launch_measure_xi(const RealView &v, const double *kcos, const doubl
                               cudaStream_t st);
 cudaError_t launch_to_natural(const RealView &v, int32_t R, bool bitpack, int8_t *out, cudaStream_t st);
 cudaError_t launch_from_natural(const RealView &v, int32_t R, bool bitpack, const int8_t *in, cudaStream_t st);
-cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st);
+// Per-(replica, CTA) partial sums of the multi-CTA int8 energy reduction, owned by the caller:
+// B, M, Fi, F [R][kEnergyMaxParts], arrival counters [R] (zero between launches).
+constexpr int kEnergyMaxParts = 16;
+struct EnergyParts {
+  long long *B, *M, *Fi;
+  double *F;
+  unsigned int *count;
+};
+// E and M of every replica (Eq. 1) into v.E, v.M.  With ep (int8 layout, L % 16 == 0) the
+// reduction spreads each replica over several CTAs; the last to arrive adds the partials in a
+// fixed order.
+cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st,
+                          const EnergyParts *ep = nullptr);
 
 // kernels_int8.cu
 cudaError_t launch_halfsweep_int8(const RealView &v, int colour, uint32_t sweep, cudaStream_t st);

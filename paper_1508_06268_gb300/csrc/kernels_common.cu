@@ -1,5 +1,6 @@
 // Set-up, energy, exchange and conversion kernels shared by both spin layouts.
 #include <cmath>
+#include <algorithm>
 #include <cstdint>
 
 #include "exchange.cuh"
@@ -262,6 +263,110 @@ __global__ void k_energy_int8_rows(RealView v, double J, double h) {
   }
 }
 
+// The same energies with eight sites per thread (64-bit words, L % 16 == 0) and each replica
+// spread over gridDim.x CTAs of one grid row: partial sums per (replica, CTA), then the last CTA
+// of the replica to arrive adds them in CTA order, so the result does not depend on which one
+// that is.  B, M and the bimodal field count are exact integers; the float field term is an
+// error-free running sum per thread (as above), added in double in a fixed order.
+template <int LC>
+__global__ void __launch_bounds__(256) k_energy_int8_rows8(RealView v, double J, double h, EnergyParts ep) {
+  const int32_t r = blockIdx.y, part = blockIdx.x, nparts = gridDim.x;
+  const int32_t L = LC ? LC : v.L, Lh = L / 2;
+  const int32_t half = L * L * Lh, plane = L * Lh, groups = half / 8;
+  const uint8_t *S0 = v.spins8 + (int64_t)r * 2 * half, *S1 = S0 + half;
+  auto ld = [](const uint8_t *p) { return *reinterpret_cast<const uint64_t *>(p); };
+  long long B = 0, M = 0, Fi = 0;
+  float fs = 0.0f, fe = 0.0f;
+  for (int32_t c = 0; c < 2; ++c) {
+    const uint8_t *S = c ? S1 : S0;
+    for (int32_t g = part * blockDim.x + threadIdx.x; g < groups; g += nparts * blockDim.x) {
+      const int32_t q0 = 8 * g;
+      const uint64_t self = ld(S + q0);
+      M += 2 * __popcll(self) - 8;
+      if (c == 0) {
+        // colour-0 sites with their six colour-1 neighbours: every bond once
+        const int32_t xh0 = q0 % Lh;
+        const int32_t row = q0 / Lh;
+        const int32_t y = row % L, z = row / L;
+        const bool par = ((y + z) & 1) != 0;
+        const uint64_t w0 = ld(S1 + q0);
+        const int32_t xa = par ? (xh0 + 8 == Lh ? 0 : xh0 + 8) : (xh0 == 0 ? Lh - 8 : xh0 - 8);
+        const uint64_t wa = ld(S1 + (q0 - xh0) + xa);
+        const uint64_t wx = par ? ((w0 >> 8) | (wa << 56)) : ((w0 << 8) | (wa >> 56));
+        const uint64_t wyp = ld(S1 + (y == L - 1 ? q0 + Lh - plane : q0 + Lh));
+        const uint64_t wym = ld(S1 + (y == 0 ? q0 - Lh + plane : q0 - Lh));
+        const uint64_t wzp = ld(S1 + (z == L - 1 ? q0 + plane - half : q0 + plane));
+        const uint64_t wzm = ld(S1 + (z == 0 ? q0 - plane + half : q0 - plane));
+        B += 48 - 2 * (__popcll(self ^ w0) + __popcll(self ^ wx) + __popcll(self ^ wyp) + __popcll(self ^ wym) +
+                       __popcll(self ^ wzp) + __popcll(self ^ wzm));
+      }
+      if (v.kind == kBimodal) {
+        Fi += 8 - 2 * __popcll(self ^ ld(v.hbit_c + c * half + q0));
+      } else {
+        const float4 *hp = reinterpret_cast<const float4 *>(v.hh_c + c * half + q0);
+        const float4 ha = hp[0], hb = hp[1];
+        const float hk[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float term = ((self >> (8 * j)) & 1u) ? hk[j] : -hk[j];
+          const float t = __fadd_rn(fs, term);
+          const float bp = __fsub_rn(t, fs);
+          const float err = __fadd_rn(__fsub_rn(fs, __fsub_rn(t, bp)), __fsub_rn(term, bp));
+          fs = t;
+          fe = __fadd_rn(fe, err);
+        }
+      }
+    }
+  }
+  double F = (double)fs + (double)fe;
+  __shared__ long long sB[8], sM[8], sF[8];
+  __shared__ double sD[8];
+  B = warp_sum(B);
+  M = warp_sum(M);
+  Fi = warp_sum(Fi);
+  F = warp_sum(F);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    sB[wid] = B;
+    sM[wid] = M;
+    sF[wid] = Fi;
+    sD[wid] = F;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tb = 0, tm = 0, tf = 0;
+    double td = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      tb += sB[w];
+      tm += sM[w];
+      tf += sF[w];
+      td += sD[w];
+    }
+    const int64_t slot = (int64_t)r * kEnergyMaxParts + part;
+    ep.B[slot] = tb;
+    ep.M[slot] = tm;
+    ep.Fi[slot] = tf;
+    ep.F[slot] = td;
+    __threadfence();
+    if (atomicAdd(ep.count + r, 1u) == (unsigned)(nparts - 1)) {
+      __threadfence();
+      tb = tm = tf = 0;
+      td = 0.0;
+      for (int q = 0; q < nparts; ++q) {
+        const int64_t s2 = (int64_t)r * kEnergyMaxParts + q;
+        tb += __ldcg(ep.B + s2);
+        tm += __ldcg(ep.M + s2);
+        tf += __ldcg(ep.Fi + s2);
+        td += __ldcg(ep.F + s2);
+      }
+      const double Fv = v.kind == kBimodal ? h * (double)tf : td;
+      v.E[r] = -J * (double)tb - Fv;
+      v.M[r] = tm;
+      ep.count[r] = 0u;
+    }
+  }
+}
+
 // Structure factor F of the correlation length (Sec. 7; the spins s_i read for the printed h_i)
 // of every replica, added to the accumulator of the replica's temperature after an exchange step:
 // F = (1 / 3N) sum over the axes d of |sum_i s_i e^{i K i_d}|^2, K = 2 pi / L.  One CTA per
@@ -424,7 +529,21 @@ cudaError_t launch_init_spins(const RealView &v, int32_t R, uint32_t stage, bool
   return cudaGetLastError();
 }
 
-cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st) {
+cudaError_t launch_energy(const RealView &v, double J, double h, bool bitpack, cudaStream_t st,
+                          const EnergyParts *ep) {
+  if (!bitpack && ep && v.L % 16 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
+    // about 2048 threads' worth of eight-site groups per CTA, at most kEnergyMaxParts CTAs per replica
+    const int64_t groups = (int64_t)v.N / 16;
+    const int parts = (int)std::min<int64_t>(kEnergyMaxParts, std::max<int64_t>(1, groups / 2048));
+    const dim3 grid((unsigned)parts, (unsigned)v.R);
+    switch (v.L) {
+      case 16: k_energy_int8_rows8<16><<<grid, 256, 0, st>>>(v, J, h, *ep); break;
+      case 32: k_energy_int8_rows8<32><<<grid, 256, 0, st>>>(v, J, h, *ep); break;
+      case 64: k_energy_int8_rows8<64><<<grid, 256, 0, st>>>(v, J, h, *ep); break;
+      default: k_energy_int8_rows8<0><<<grid, 256, 0, st>>>(v, J, h, *ep); break;
+    }
+    return cudaGetLastError();
+  }
   if (!bitpack && v.L % 8 == 0 && (int64_t)v.N / 2 < ((int64_t)1 << 31)) {
     switch (v.L) {
       case 16: k_energy_int8_rows<16><<<v.R, 1024, 0, st>>>(v, J, h); break;

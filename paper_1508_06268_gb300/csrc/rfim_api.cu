@@ -43,6 +43,7 @@ struct rfim_ctx {
   double *obs = nullptr;
   int64_t *n_meas = nullptr;
   int8_t *scratch8 = nullptr;  // int8[Rcap][N] staging for state conversion
+  EnergyParts eparts{};        // int8 layout: partials of the multi-CTA energy reduction
   // structure-factor measurement (correlation length, Sec. 7): off unless enabled
   bool xi_on = false;
   double *sumF = nullptr, *kcos = nullptr, *ksin = nullptr;
@@ -146,7 +147,8 @@ void free_all(rfim_ctx *c) {
   free_events(c);
   void *ptrs[] = {c->spins8, c->bits, c->hraw, c->hh_c, c->hbit_c, c->hbits, c->thr, c->gjn, c->b2, c->b2l,
                   c->beta_d, c->t2r, c->r2t, c->E, c->M, c->att, c->acc, c->obs, c->n_meas, c->scratch8,
-                  c->sumF, c->kcos, c->ksin};
+                  c->sumF, c->kcos, c->ksin, c->eparts.B, c->eparts.M, c->eparts.Fi, c->eparts.F,
+                  c->eparts.count};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   free_bits_plan(c->plan);
@@ -254,7 +256,8 @@ int do_exchange(rfim_ctx *c, int64_t measure_from) {
   RealView v = view_of(c);
   cudaEvent_t stop;
   CUDA_OR_FAIL(c, prof_begin(c, 1, &stop));
-  CUDA_OR_FAIL(c, launch_energy(v, (double)c->J, (double)c->h, c->layout == RFIM_LAYOUT_BITPACK, c->stream));
+  CUDA_OR_FAIL(c, launch_energy(v, (double)c->J, (double)c->h, c->layout == RFIM_LAYOUT_BITPACK, c->stream,
+                                 c->eparts.count ? &c->eparts : nullptr));
   CUDA_OR_FAIL(c, launch_exchange(v, (uint32_t)c->xstep, measure_from, c->stream));
   CUDA_OR_FAIL(c, prof_end(c, stop));
   c->launches += 2;
@@ -363,6 +366,14 @@ int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
     if ((rc = dalloc(c, &c->hbits, N / 32))) return bail(rc);
   } else {
     if ((rc = dalloc(c, &c->spins8, (size_t)Rcap * N))) return bail(rc);
+    const size_t parts = (size_t)Rcap * kEnergyMaxParts;
+    if ((rc = dalloc(c, &c->eparts.B, parts))) return bail(rc);
+    if ((rc = dalloc(c, &c->eparts.M, parts))) return bail(rc);
+    if ((rc = dalloc(c, &c->eparts.Fi, parts))) return bail(rc);
+    if ((rc = dalloc(c, &c->eparts.F, parts))) return bail(rc);
+    if ((rc = dalloc(c, &c->eparts.count, (size_t)Rcap))) return bail(rc);
+    const cudaError_t e = cudaMemsetAsync(c->eparts.count, 0, (size_t)Rcap * 4, c->stream);
+    if (e != cudaSuccess) return bail(fail(c, RFIM_ECUDA, "memset: %s", cudaGetErrorString(e)));
   }
   if ((rc = dalloc(c, &c->hraw, N))) return bail(rc);
   if ((rc = dalloc(c, &c->hh_c, N))) return bail(rc);
@@ -645,7 +656,8 @@ int rfim_get_state(rfim_ctx *ctx, int8_t *spins, int32_t *t2r, double *E, int64_
   if (t2r) CUDA_OR_FAIL(c, cudaMemcpyAsync(t2r, c->t2r, c->R * 4, cudaMemcpyDeviceToHost, c->stream));
   if (E) {
     // recompute from the current spins into the energy buffer, then read it
-    CUDA_OR_FAIL(c, launch_energy(v, (double)c->J, (double)c->h, c->layout == RFIM_LAYOUT_BITPACK, c->stream));
+    CUDA_OR_FAIL(c, launch_energy(v, (double)c->J, (double)c->h, c->layout == RFIM_LAYOUT_BITPACK, c->stream,
+                                 c->eparts.count ? &c->eparts : nullptr));
     c->launches += 1;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(E, c->E, c->R * 8, cudaMemcpyDeviceToHost, c->stream));
   }
