@@ -519,3 +519,23 @@ def test_multihit_settings_checked_at_the_boundary():
     with pytest.raises(rf.RfimError):
         gi.set_multihit(1, 8)
     g.set_multihit(0)
+
+
+def test_multihit_adaptation_bit_exact_bimodal():
+    """Adaptive temperature trials (Sec. 4) run with multi-hit sweeps: the adapted set, the trial
+    rates and the final state equal the oracle's."""
+    L, R0, trials, a = 16, 4, 2, 1
+    temps = inputs.geometric_temps(1.0, 5.0, R0)
+    g, o = make_pair(L, temps, kind=BIM, layout=BP, h=1.5, R_capacity=R0 + trials * a)
+    g.set_multihit(2, 8)
+    o.set_multihit(2, 8)
+    Tg, rg_ = g.adapt_temps(trials, 40, 4, a, return_rates=True)
+    Ro, ro_ = o.adapt(trials, 40, 4, a, return_rates=True)
+    assert g.R == Ro == R0 + trials * a
+    np.testing.assert_array_equal(Tg, o.temps())
+    np.testing.assert_array_equal(rg_, ro_)
+    g.run(8, 4, 0)
+    o.run(8, 4, 0)
+    assert_same_state(g, o, "after adaptation with multi-hit sweeps")
+    E = g.get_state(spins=False, t2r=False, energies=True)["E"]
+    np.testing.assert_array_equal(E, np.array([o.energy(r)[0] for r in range(g.R)]))
