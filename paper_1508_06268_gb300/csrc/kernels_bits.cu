@@ -156,6 +156,7 @@ MultiHit make_multihit(int32_t L, int32_t mh, int32_t tile) {
   if (mh <= 0 || !multihit_tile_ok(L, tile)) return m;
   m.mh = mh;
   m.tile = tile;
+  while ((1 << m.tile_log2) < tile) ++m.tile_log2;
   for (int j = 0; j < 8; ++j)
     if ((((8 * j) % L) / tile) & 1) m.odd_tx |= 1u << j;
   return m;

@@ -45,7 +45,9 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
 
   const int ngroups = (gact + GT - 1) / GT;
   const int items = WC * ngroups;
-  const int T = mh.tile, wpt = T / RW;  // words of one tile band (T rows) in a plane
+  // tiles and bands are powers of two: words of one tile band (T rows) in a plane = T / RW
+  constexpr int RW_LOG2 = RW == 1 ? 0 : RW == 2 ? 1 : 2;
+  const int t_log2 = mh.tile_log2, w_log2 = t_log2 - RW_LOG2, wmask = (1 << w_log2) - 1;
   for (int s = 0; s < nsw; ++s) {
     const uint32_t sweep = sweep0 + (uint32_t)s;
 #pragma unroll 1
@@ -59,13 +61,13 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
 #pragma unroll 1
           for (int item = tid; item < items; item += nt) {
             // item -> (replica group, parity class of y/T + z/T, word): each class holds WC / 2
-            // words of the slab, P / 2 per plane, in bands of wpt words of alternate tile rows
+            // words of the slab, P / 2 per plane, in bands of T / RW words of alternate tile rows
             const int grp = item / WC, k = item % WC;
             const int cls = k / (WC / 2), kk = k % (WC / 2);
             const int zl = kk / (P / 2), idx = kk % (P / 2);
             const int z = z0 + zl;
-            const int typar = (cls ^ (z / T)) & 1;
-            const int iw = (2 * (idx / wpt) + typar) * wpt + idx % wpt;
+            const int typar = (cls ^ (z >> t_log2)) & 1;
+            const int iw = ((2 * (idx >> w_log2) + typar) << w_log2) + (idx & wmask);
             const int wl = zl * P + iw;
             const int64_t wq = (int64_t)z * P + iw;
             // blocks in tiles of the visited coarse colour: tile x parity = coarse xor class

@@ -37,7 +37,7 @@ struct BitsPlan {
 struct MultiHit {
   int32_t mh = 0, tile = 0;
   uint32_t odd_tx = 0u;
-  int32_t pad = 0;
+  int32_t tile_log2 = 0;
 };
 // Whether tiles of edge `tile` are supported at L; the setting for (L, mh, tile).
 bool multihit_tile_ok(int32_t L, int32_t tile);
