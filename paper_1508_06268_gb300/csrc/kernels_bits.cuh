@@ -444,6 +444,93 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
 }
 
 
+// Metropolis update of one word (32 sites of colour c at plane zl, word iw of the slab) in the GT
+// replicas of group grp: neighbour counts from the other colour's words, one Philox block per
+// (block j, replica) with counter (8 wq + j, r, ctr2, tag), decisions, and the flipped words
+// written back.  MASKED: only the blocks with their bit set in amask (warp-uniform) are updated.
+// Replicas past the end of a partial group repeat the last one; only their write is skipped.
+template <int L, int S, int GT, bool BIM, bool MASKED>
+__device__ __forceinline__ void update_word(const RealView &v, uint32_t *sp, int c, int zl, int iw, int z0, int grp,
+                                            int gact, int r0, uint32_t ctr2, uint32_t tag, uint32_t slot0,
+                                            const float4 *__restrict__ field4, int up_rank, int dn_rank,
+                                            uint32_t amask) {
+  using Gm = BitsGeom<L>;
+  constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
+  constexpr int64_t WPAD = (W + 31) / 32 * 32;
+  const int wl = zl * P + iw, z = z0 + zl;
+  const int64_t wq = (int64_t)z * P + iw;
+  float4 hh4[8] = {};
+  if (!BIM) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (!MASKED || ((amask >> j) & 1u)) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
+  }
+  const uint32_t p0 = parity0_mask<L>(c, z, iw);
+  uint32_t c0[GT], c1[GT], c2[GT], sf[GT], flip[GT];
+#pragma unroll
+  for (int gg = 0; gg < GT; ++gg) {
+    const int g = min(grp * GT + gg, gact - 1);
+    uint32_t nb[6];
+    neighbour_words<L, S>(sp + ((size_t)g * 2 + (c ^ 1)) * WC, zl, iw, p0, up_rank, dn_rank, nb);
+    count6(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], c0[gg], c1[gg], c2[gg]);
+    sf[gg] = sp[((size_t)g * 2 + c) * WC + wl];
+    flip[gg] = 0u;
+  }
+  const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+  PairSlices ps[GT];
+#pragma unroll
+  for (int gg = 0; gg < GT; ++gg) ps[gg] = make_pairs(c0[gg], c1[gg], c2[gg], sf[gg], fb);
+  // float field: flip = fk[k] << 8k once all blocks are done
+  uint32_t fk[GT][4];
+#pragma unroll
+  for (int gg = 0; gg < GT; ++gg)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fk[gg][k] = 0u;
+#pragma unroll kBlockUnroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int j = 7 - jj;
+    if (!MASKED || ((amask >> j) & 1u)) {
+#pragma unroll
+      for (int gg = 0; gg < GT; ++gg) {
+        const int g = min(grp * GT + gg, gact - 1);
+        const Words4 w = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), ctr2, tag);
+        decide_block<BIM>(w, ps[gg], j, slot0 + (uint32_t)g * kTabSlot, hh4[j], flip[gg], fk[gg]);
+      }
+    } else if (!BIM) {
+      // keep block j's sign bits at bit j of fk: a skipped block shifts in zeros
+#pragma unroll
+      for (int gg = 0; gg < GT; ++gg)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fk[gg][k] <<= 1;
+    }
+  }
+  if (!BIM) {
+#pragma unroll
+    for (int gg = 0; gg < GT; ++gg) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
+  }
+#pragma unroll
+  for (int gg = 0; gg < GT; ++gg) {
+    const int g = grp * GT + gg;
+    if (GT > 1 && g >= gact) continue;
+    sp[((size_t)g * 2 + c) * WC + wl] = sf[gg] ^ flip[gg];
+  }
+}
+
+// Copies the slab (both colours) of replicas [r0, r0 + gact) between global and shared memory.
+template <int L, int S, bool TO_SHARED>
+__device__ __forceinline__ void copy_slab(const RealView &v, uint32_t *sp, int r0, int gact, int z0) {
+  using Gm = BitsGeom<L>;
+  constexpr int P = Gm::P, W = Gm::W, WC = (L / S) * P;
+  for (int t = threadIdx.x; t < gact * 2 * WC; t += blockDim.x) {
+    const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
+    uint32_t *gw = v.bits + ((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl;
+    if (TO_SHARED)
+      sp[t] = *gw;
+    else
+      *gw = sp[t];
+  }
+}
+
 // One exchange interval of replicas [r0, r0 + gact) of realization v, slab `rank` of S: load into
 // shared memory, nsw sweeps, write back, and (xa.enabled) the energy partials and the exchange
 // tail.  All threads of the CTA call it; blockDim.x threads, dynamic shared memory >= the plan's.
@@ -476,6 +563,9 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)c);
+      // the word update is written out here rather than called through update_word (which the
+      // multi-hit kernel uses): the call changes the register allocation of this kernel (100 ->
+      // 128 registers with spills for the float field at L = 64)
 #pragma unroll 1
       for (int item = tid; item < items; item += nt) {
         const int wl = item % WC, grp = item / WC;

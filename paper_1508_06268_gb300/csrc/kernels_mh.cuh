@@ -23,9 +23,8 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
                                                  int nsw, const float4 *__restrict__ field4, const ExchArgs &xa,
                                                  const MultiHit &mh) {
   using Gm = BitsGeom<L>;
-  constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
+  constexpr int P = Gm::P, PZ = L / S, WC = PZ * P;
   constexpr int RW = 64 / L;  // rows of one colour held by a word
-  constexpr int64_t WPAD = (W + 31) / 32 * 32;
   static_assert(L >= 16 && WC % 64 == 0, "a warp's words must share one parity class");
   extern __shared__ __align__(16) uint32_t sm[];
   const int up_rank = (rank + 1) % S, dn_rank = (rank + S - 1) % S;
@@ -36,10 +35,7 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
   const uint32_t slot0 = tab_slot0(tab);
   const int nt = blockDim.x, tid = threadIdx.x;
 
-  for (int t = tid; t < gact * 2 * WC; t += nt) {
-    const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
-    sp[t] = v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl];
-  }
+  copy_slab<L, S, true>(v, sp, r0, gact, z0);
   tab_fill<BIM>(v, tab, slot0, gact, [&](int g) { return r0 + g; });
   sync_slabs<S>();
 
@@ -68,65 +64,10 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
             const int z = z0 + zl;
             const int typar = (cls ^ (z >> t_log2)) & 1;
             const int iw = ((2 * (idx >> w_log2) + typar) << w_log2) + (idx & wmask);
-            const int wl = zl * P + iw;
-            const int64_t wq = (int64_t)z * P + iw;
             // blocks in tiles of the visited coarse colour: tile x parity = coarse xor class
             const uint32_t amask = ((coarse ^ cls) & 1) ? mh.odd_tx : (~mh.odd_tx & 0xFFu);
-            float4 hh4[8] = {};
-            if (!BIM) {
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if ((amask >> j) & 1u) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
-            }
-            const uint32_t p0 = parity0_mask<L>(c, z, iw);
-            uint32_t c0[GT], c1[GT], c2w[GT], sf[GT], flip[GT];
-#pragma unroll
-            for (int gg = 0; gg < GT; ++gg) {
-              const int g = min(grp * GT + gg, gact - 1);
-              uint32_t nb[6];
-              neighbour_words<L, S>(sp + ((size_t)g * 2 + (c ^ 1)) * WC, zl, iw, p0, up_rank, dn_rank, nb);
-              count6(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], c0[gg], c1[gg], c2w[gg]);
-              sf[gg] = sp[((size_t)g * 2 + c) * WC + wl];
-              flip[gg] = 0u;
-            }
-            const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
-            PairSlices ps[GT];
-#pragma unroll
-            for (int gg = 0; gg < GT; ++gg) ps[gg] = make_pairs(c0[gg], c1[gg], c2w[gg], sf[gg], fb);
-            uint32_t fk[GT][4];
-#pragma unroll
-            for (int gg = 0; gg < GT; ++gg)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) fk[gg][q] = 0u;
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int j = 7 - jj;
-              if ((amask >> j) & 1u) {
-#pragma unroll
-                for (int gg = 0; gg < GT; ++gg) {
-                  const int g = min(grp * GT + gg, gact - 1);
-                  const Words4 w = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), c2, tag);
-                  decide_block<BIM>(w, ps[gg], j, slot0 + (uint32_t)g * kTabSlot, hh4[j], flip[gg], fk[gg]);
-                }
-              } else if (!BIM) {
-                // keep block j's sign bits at bit j of fk: a skipped block shifts in zeros
-#pragma unroll
-                for (int gg = 0; gg < GT; ++gg)
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) fk[gg][q] <<= 1;
-              }
-            }
-            if (!BIM) {
-#pragma unroll
-              for (int gg = 0; gg < GT; ++gg)
-                flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
-            }
-#pragma unroll
-            for (int gg = 0; gg < GT; ++gg) {
-              const int g = grp * GT + gg;
-              if (GT > 1 && g >= gact) continue;
-              sp[((size_t)g * 2 + c) * WC + wl] = sf[gg] ^ flip[gg];
-            }
+            update_word<L, S, GT, BIM, true>(v, sp, c, zl, iw, z0, grp, gact, r0, c2, tag, slot0, field4, up_rank,
+                                             dn_rank, amask);
           }
           sync_slabs<S>();
         }
@@ -134,10 +75,7 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
     }
   }
 
-  for (int t = tid; t < gact * 2 * WC; t += nt) {
-    const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
-    v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl] = sp[t];
-  }
+  copy_slab<L, S, false>(v, sp, r0, gact, z0);
   if (xa.enabled) interval_tail<L, S, BIM>(v, G, r0, gact, rank, nsw, field4, xa);
 }
 
