@@ -124,3 +124,20 @@ def test_errors_at_the_boundary():
         with pytest.raises(rf.RfimError) as e:
             srv.wait(t, timeout_s=60)
         assert e.value.code == rf.ENOMEM
+
+
+def test_served_maximum_replica_count_equals_oracle():
+    """The largest served temperature set (R = 1024, L = 8: 64 replica groups of 16) with the
+    structure factor measured: observables, exchange statistics and F sums equal the oracle's."""
+    L, R, real = 8, 1024, 3
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    with rf.Server(mem_budget_bytes=64 << 20, max_slots=2, measure_xi=True) as srv:
+        res = srv.wait(submit(srv, L, R, rf.FIELD_BIMODAL, real, sweeps=20))
+    o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=10 + real, seed=42,
+                      realization=real)
+    o.set_measure_xi(True)
+    o.run(20, EX, 1)
+    np.testing.assert_array_equal(res["sums"], o.observables())
+    att, acc = o.exchange_stats()
+    np.testing.assert_array_equal(res["acc"], acc)
+    np.testing.assert_allclose(res["F"], o.observables_F(), rtol=1e-11, atol=1e-20)
