@@ -539,3 +539,16 @@ def test_multihit_adaptation_bit_exact_bimodal():
     assert_same_state(g, o, "after adaptation with multi-hit sweeps")
     E = g.get_state(spins=False, t2r=False, energies=True)["E"]
     np.testing.assert_array_equal(E, np.array([o.energy(r)[0] for r in range(g.R)]))
+
+
+def test_multihit_full_size_bit_exact():
+    """Multi-hit sweeps at the benchmark shape (L = 64, R = 128, the cluster plan the multi-hit
+    workload times), two sweeps with an exchange step after each."""
+    temps = inputs.geometric_temps(1.0, 5.0, 128)
+    g, o = make_pair(64, temps, kind=BIM, layout=BP, h=1.0, field_seed=2, seed=42)
+    g.set_multihit(2, 8)
+    o.set_multihit(2, 8)
+    g.run(2, 1, 0)
+    o.run(2, 1, 0)
+    assert_same_state(g, o, "multi-hit at full size")
+    np.testing.assert_array_equal(g.observables()["sums"], o.observables())
