@@ -141,3 +141,20 @@ def test_served_maximum_replica_count_equals_oracle():
     att, acc = o.exchange_stats()
     np.testing.assert_array_equal(res["acc"], acc)
     np.testing.assert_allclose(res["F"], o.observables_F(), rtol=1e-11, atol=1e-20)
+
+
+def test_served_full_size_equals_oracle():
+    """A served realization of the largest C5 shape (L = 64, R = 128: 64 work items of two
+    replicas) with the structure factor measured equals the oracle."""
+    L, R, real = 64, 128, 5
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    with rf.Server(mem_budget_bytes=256 << 20, max_slots=2, measure_xi=True) as srv:
+        res = srv.wait(srv.submit(L, temps, 4, 2, 1, field_kind=rf.FIELD_BIMODAL, h=1.5, field_seed=10 + real,
+                                  seed=42, realization=real))
+    o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=10 + real, seed=42,
+                      realization=real)
+    o.set_measure_xi(True)
+    o.run(4, 2, 1)
+    np.testing.assert_array_equal(res["sums"], o.observables())
+    np.testing.assert_array_equal(res["acc"], o.exchange_stats()[1])
+    np.testing.assert_allclose(res["F"], o.observables_F(), rtol=1e-11, atol=1e-20)
