@@ -60,16 +60,19 @@ KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
 
 using MhFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *, ExchArgs, MultiHit);
 
-template <int L, int S, int GT, int NT>
+template <int L, int S, int GT, int NT, int T>
 MhFn mh_pick(bool bim) {
-  return bim ? (MhFn)k_sweeps_bits_mh<L, S, GT, true, NT> : (MhFn)k_sweeps_bits_mh<L, S, GT, false, NT>;
+  return bim ? (MhFn)k_sweeps_bits_mh<L, S, GT, true, NT, T> : (MhFn)k_sweeps_bits_mh<L, S, GT, false, NT, T>;
 }
 
-// Multi-hit instances: the default cluster / single-CTA shapes of L = 64, 32, 16.
-MhFn mh_kernel_for(int L, int S, int GT, int NT, bool bim) {
-  if (L == 64 && S == 4 && GT == 4 && NT == 512) return mh_pick<64, 4, 4, 512>(bim);
-  if (L == 32 && S == 2 && GT == 1 && NT == 256) return mh_pick<32, 2, 1, 256>(bim);
-  if (L == 16 && S == 1 && GT == 1 && NT == 512) return mh_pick<16, 1, 1, 512>(bim);
+// Multi-hit instances: the default cluster / single-CTA shapes of L = 64, 32, 16, per tile edge.
+MhFn mh_kernel_for(int L, int S, int GT, int NT, bool bim, int T) {
+  if (L == 64 && S == 4 && GT == 4 && NT == 512)
+    return T == 8 ? mh_pick<64, 4, 4, 512, 8>(bim) : T == 16 ? mh_pick<64, 4, 4, 512, 16>(bim)
+                                                   : T == 32 ? mh_pick<64, 4, 4, 512, 32>(bim) : nullptr;
+  if (L == 32 && S == 2 && GT == 1 && NT == 256)
+    return T == 8 ? mh_pick<32, 2, 1, 256, 8>(bim) : T == 16 ? mh_pick<32, 2, 1, 256, 16>(bim) : nullptr;
+  if (L == 16 && S == 1 && GT == 1 && NT == 512) return T == 8 ? mh_pick<16, 1, 1, 512, 8>(bim) : nullptr;
   return nullptr;
 }
 
@@ -156,20 +159,21 @@ MultiHit make_multihit(int32_t L, int32_t mh, int32_t tile) {
   if (mh <= 0 || !multihit_tile_ok(L, tile)) return m;
   m.mh = mh;
   m.tile = tile;
-  while ((1 << m.tile_log2) < tile) ++m.tile_log2;
-  for (int j = 0; j < 8; ++j)
-    if ((((8 * j) % L) / tile) & 1) m.odd_tx |= 1u << j;
   return m;
 }
 
 cudaError_t prepare_multihit(const BitsPlan &plan, bool bimodal) {
   if (plan.S == 0) return cudaErrorInvalidConfiguration;
-  MhFn fn = mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, bimodal);
-  if (!fn) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
-  if (e == cudaSuccess && plan.S > 1)
-    e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  return e;
+  for (int T : {8, 16, 32}) {
+    if (!multihit_tile_ok(plan.L, T)) continue;
+    MhFn fn = mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, bimodal, T);
+    if (!fn) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (e == cudaSuccess && plan.S > 1)
+      e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 namespace {
@@ -397,7 +401,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   const bool multihit = mh && mh->mh > 0;
   if (multihit && plan.S == 0) return cudaErrorInvalidConfiguration;
   KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
-  MhFn mfn = multihit ? mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal) : nullptr;
+  MhFn mfn = multihit ? mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, mh->tile) : nullptr;
   if (!fn && !mfn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;
   cudaLaunchConfig_t cfg = {};

@@ -444,16 +444,34 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
 }
 
 
+// Per byte, bit b of the low nibble moves to the b-th set bit of PAT (four set bits).
+template <uint32_t PAT>
+__device__ __forceinline__ uint32_t deposit_nibbles(uint32_t x) {
+  uint32_t out = 0u;
+  int b = 0;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    if ((PAT >> p) & 1u) {
+      const uint32_t moved = p >= b ? x << (p - b) : x >> (b - p);
+      out |= moved & (0x01010101u << p);
+      ++b;
+    }
+  }
+  return out;
+}
+
 // Metropolis update of one word (32 sites of colour c at plane zl, word iw of the slab) in the GT
 // replicas of group grp: neighbour counts from the other colour's words, one Philox block per
 // (block j, replica) with counter (8 wq + j, r, ctr2, tag), decisions, and the flipped words
-// written back.  MASKED: only the blocks with their bit set in amask (warp-uniform) are updated.
-// Replicas past the end of a partial group repeat the last one; only their write is skipped.
-template <int L, int S, int GT, bool BIM, bool MASKED>
+// written back.  Only the blocks with their bit set in PAT are updated (0xFF: all; otherwise four
+// of them, whose float-field sign bits are collected side by side and then moved to their bytes'
+// bit j).  Replicas past the end of a partial group repeat the last one; only their write is
+// skipped.
+template <int L, int S, int GT, bool BIM, uint32_t PAT>
 __device__ __forceinline__ void update_word(const RealView &v, uint32_t *sp, int c, int zl, int iw, int z0, int grp,
                                             int gact, int r0, uint32_t ctr2, uint32_t tag, uint32_t slot0,
-                                            const float4 *__restrict__ field4, int up_rank, int dn_rank,
-                                            uint32_t amask) {
+                                            const float4 *__restrict__ field4, int up_rank, int dn_rank) {
+  static_assert(PAT == 0xFFu || __builtin_popcount(PAT) == 4, "a pass updates all blocks or four of them");
   using Gm = BitsGeom<L>;
   constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
@@ -463,7 +481,7 @@ __device__ __forceinline__ void update_word(const RealView &v, uint32_t *sp, int
   if (!BIM) {
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      if (!MASKED || ((amask >> j) & 1u)) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
+      if ((PAT >> j) & 1u) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
   }
   const uint32_t p0 = parity0_mask<L>(c, z, iw);
   uint32_t c0[GT], c1[GT], c2[GT], sf[GT], flip[GT];
@@ -489,24 +507,21 @@ __device__ __forceinline__ void update_word(const RealView &v, uint32_t *sp, int
 #pragma unroll kBlockUnroll
   for (int jj = 0; jj < 8; ++jj) {
     const int j = 7 - jj;
-    if (!MASKED || ((amask >> j) & 1u)) {
+    if ((PAT >> j) & 1u) {
 #pragma unroll
       for (int gg = 0; gg < GT; ++gg) {
         const int g = min(grp * GT + gg, gact - 1);
         const Words4 w = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), ctr2, tag);
         decide_block<BIM>(w, ps[gg], j, slot0 + (uint32_t)g * kTabSlot, hh4[j], flip[gg], fk[gg]);
       }
-    } else if (!BIM) {
-      // keep block j's sign bits at bit j of fk: a skipped block shifts in zeros
-#pragma unroll
-      for (int gg = 0; gg < GT; ++gg)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) fk[gg][k] <<= 1;
     }
   }
   if (!BIM) {
 #pragma unroll
-    for (int gg = 0; gg < GT; ++gg) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
+    for (int gg = 0; gg < GT; ++gg) {
+      flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
+      if (PAT != 0xFFu) flip[gg] = deposit_nibbles<PAT>(flip[gg]);
+    }
   }
 #pragma unroll
   for (int gg = 0; gg < GT; ++gg) {

@@ -8,8 +8,8 @@
 // The whole slab already sits in shared memory, so a tile visit needs no load of its own: a pass
 // is a masked half-sweep.  With T a multiple of 8, the four sites of a Philox block (x in
 // [8 j', 8 j' + 8) of one row) lie in one tile, so a pass skips whole blocks.  Words are handed
-// to threads grouped by the parity of (y/T + z/T), so the 32 words of a warp skip the same
-// blocks and the skip is a uniform branch.
+// to threads grouped by the parity of (y/T + z/T), so the 32 words of a warp update the same
+// blocks; the tile edge is a template parameter, so which blocks is known at compile time.
 #pragma once
 #include <cstdint>
 
@@ -18,7 +18,15 @@
 
 namespace rfim {
 
-template <int L, int S, int GT, bool BIM>
+// Blocks j of a word (x in [8 j mod L, 8 j mod L + 8)) that lie in tiles of odd x index.
+__host__ __device__ constexpr uint32_t odd_tile_blocks(int L, int T) {
+  uint32_t m = 0u;
+  for (int j = 0; j < 8; ++j)
+    if ((((8 * j) % L) / T) & 1) m |= 1u << j;
+  return m;
+}
+
+template <int L, int S, int GT, bool BIM, int T>
 __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r0, int gact, int rank, uint32_t sweep0,
                                                  int nsw, const float4 *__restrict__ field4, const ExchArgs &xa,
                                                  const MultiHit &mh) {
@@ -41,9 +49,10 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
 
   const int ngroups = (gact + GT - 1) / GT;
   const int items = WC * ngroups;
-  // tiles and bands are powers of two: words of one tile band (T rows) in a plane = T / RW
-  constexpr int RW_LOG2 = RW == 1 ? 0 : RW == 2 ? 1 : 2;
-  const int t_log2 = mh.tile_log2, w_log2 = t_log2 - RW_LOG2, wmask = (1 << w_log2) - 1;
+  // words of one tile band (T rows) in a plane; blocks in tiles of odd / even x index
+  constexpr int WPT = T / RW;
+  constexpr uint32_t ODD = odd_tile_blocks(L, T), EVEN = ~ODD & 0xFFu;
+  static_assert(T % 8 == 0 && L % (2 * T) == 0 && WPT >= 1, "tiles of edge 8, 16 or 32 dividing L / 2");
   for (int s = 0; s < nsw; ++s) {
     const uint32_t sweep = sweep0 + (uint32_t)s;
 #pragma unroll 1
@@ -62,12 +71,16 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
             const int cls = k / (WC / 2), kk = k % (WC / 2);
             const int zl = kk / (P / 2), idx = kk % (P / 2);
             const int z = z0 + zl;
-            const int typar = (cls ^ (z >> t_log2)) & 1;
-            const int iw = ((2 * (idx >> w_log2) + typar) << w_log2) + (idx & wmask);
+            const int typar = (cls ^ (z / T)) & 1;
+            const int iw = (2 * (idx / WPT) + typar) * WPT + idx % WPT;
             // blocks in tiles of the visited coarse colour: tile x parity = coarse xor class
-            const uint32_t amask = ((coarse ^ cls) & 1) ? mh.odd_tx : (~mh.odd_tx & 0xFFu);
-            update_word<L, S, GT, BIM, true>(v, sp, c, zl, iw, z0, grp, gact, r0, c2, tag, slot0, field4, up_rank,
-                                             dn_rank, amask);
+            // (uniform over the warp, whose 32 words share the class)
+            if ((coarse ^ cls) & 1)
+              update_word<L, S, GT, BIM, ODD>(v, sp, c, zl, iw, z0, grp, gact, r0, c2, tag, slot0, field4, up_rank,
+                                              dn_rank);
+            else
+              update_word<L, S, GT, BIM, EVEN>(v, sp, c, zl, iw, z0, grp, gact, r0, c2, tag, slot0, field4, up_rank,
+                                               dn_rank);
           }
           sync_slabs<S>();
         }
@@ -79,14 +92,14 @@ __device__ __forceinline__ void bits_interval_mh(const RealView &v, int G, int r
   if (xa.enabled) interval_tail<L, S, BIM>(v, G, r0, gact, rank, nsw, field4, xa);
 }
 
-template <int L, int S, int GT, bool BIM, int NT>
+template <int L, int S, int GT, bool BIM, int NT, int T>
 __global__ void __launch_bounds__(NT) k_sweeps_bits_mh(RealView v, int32_t G, uint32_t sweep0, int32_t nsw,
                                                         const float4 *__restrict__ field4, ExchArgs xa, MultiHit mh) {
   const int rank = S > 1 ? (int)cluster_rank() : 0;
   const int r0 = (int)(blockIdx.x / S) * G;
   const int gact = min(G, v.R - r0);
   xa.expected = gridDim.x;
-  bits_interval_mh<L, S, GT, BIM>(v, G, r0, gact, rank, sweep0, nsw, field4, xa, mh);
+  bits_interval_mh<L, S, GT, BIM, T>(v, G, r0, gact, rank, sweep0, nsw, field4, xa, mh);
 }
 
 }  // namespace rfim

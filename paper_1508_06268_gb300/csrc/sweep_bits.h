@@ -31,13 +31,10 @@ struct BitsPlan {
 };
 
 // Multi-hit double 3D checkerboard (Sec. 3.2, kernels_mh.cuh): mh local passes per tile visit
-// (0: the plain checkerboard), tiles of edge `tile` (a multiple of 8 dividing L / 2); odd_tx has
-// bit j set when Philox block j of a word (x in [8 j mod L, 8 j mod L + 8)) lies in a tile with
-// odd x index.
+// (0: the plain checkerboard), tiles of edge `tile` (8, 16 or 32, dividing L / 2; the kernel is
+// instantiated per tile edge).
 struct MultiHit {
   int32_t mh = 0, tile = 0;
-  uint32_t odd_tx = 0u;
-  int32_t tile_log2 = 0;
 };
 // Whether tiles of edge `tile` are supported at L; the setting for (L, mh, tile).
 bool multihit_tile_ok(int32_t L, int32_t tile);
