@@ -245,10 +245,10 @@ const char *rfim_server_last_error(const rfim_server *s);
    enqueued on `stream`.  It allocates nothing: its scratch (partial sums per replica and z slab,
    and an arrival counter) is a file-scope device array of 512 KiB that every GPU loading the
    library holds until exit.  R times the number of z slabs must fit 16384 slots (RFIM_EINVAL
-   otherwise, message in rfim_last_error(NULL)).  The first call on a device sets the array up
-   (looks up its device address and clears the counter, synchronising `stream`); make that first
-   call before any stream capture.  All calls share the array, which keeps the last call's
-   contents: calls that overlap on the GPU race and must not be issued.
+   otherwise, message in rfim_last_error(NULL)).  Every call looks up the array's address on the
+   current device (cudaGetSymbolAddress, no stream work); its arrival counter is zero when the
+   library loads and each call leaves it at zero.  All calls share the array, which keeps the last
+   call's contents: calls that overlap on the GPU race and must not be issued.
    Buffers (all device pointers, caller-owned):
      spins : uint32[R][2][L^3/64] bit layout: for colour c = (x+y+z) mod 2 the site with
              q = (x>>1) + (L/2)(y + L z) is bit 8(q&3) + ((q&31)>>2) of word q>>5 (1 = up)

@@ -6,10 +6,10 @@
 //
 // The array is shared by every call on a device and keeps the last call's contents; calls that
 // overlap on the GPU (different streams, or host threads without ordering) race on it.  The
-// arrival counter starts at zero (cleared at set-up) and the last CTA of each call sets it back.
+// arrival counter starts at zero (a file-scope device array is zero when the module loads) and
+// the last CTA of each call sets it back to zero.
 #include <algorithm>
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "rfim.h"
@@ -147,10 +147,6 @@ __global__ void __launch_bounds__(256) k_exchange_noalloc(NoAllocArgs a, uint32_
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Device address of the scratch array per device, obtained once with that device current.
-std::mutex g_setup_mu;
-unsigned char *g_scratch_ptr[64] = {};
-
 }  // namespace
 
 }  // namespace rfim
@@ -172,27 +168,14 @@ extern "C" int rfim_exchange_noalloc(const rfim_exchange_buffers *b, uint32_t j,
   if (slabs < 1)
     return set_thread_error(RFIM_EINVAL, "rfim_exchange_noalloc: R exceeds the static scratch capacity (16384 replicas)");
   cudaStream_t st = (cudaStream_t)stream;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) return set_thread_error(RFIM_ECUDA, "rfim_exchange_noalloc: no device");
+  // In host code g_exchange_scratch names a host-side stand-in, not device memory: the kernel
+  // gets the array's device address on the current device, looked up on every call (no stream
+  // work; a cached address would go stale after cudaDeviceReset).
   unsigned char *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-      // set-up on this device's first call: the symbol's device address, counter cleared
-      e = cudaGetSymbolAddress((void **)&scratch, g_exchange_scratch);
-      if (e != cudaSuccess)
-        return set_thread_error(RFIM_ECUDA, std::string("rfim_exchange_noalloc: cudaGetSymbolAddress: ") +
-                                                cudaGetErrorString(e));
-      e = cudaMemsetAsync(scratch + kCounterOffset, 0, 256, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess)
-        return set_thread_error(RFIM_ECUDA, std::string("rfim_exchange_noalloc: clearing the counter: ") +
-                                                cudaGetErrorString(e));
-      g_scratch_ptr[dev] = scratch;
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress((void **)&scratch, g_exchange_scratch);
+  if (e != cudaSuccess || !scratch)
+    return set_thread_error(RFIM_ECUDA, std::string("rfim_exchange_noalloc: cudaGetSymbolAddress: ") +
+                                            cudaGetErrorString(e));
   NoAllocArgs a{};
   a.v.L = L;
   a.v.Lh = L / 2;

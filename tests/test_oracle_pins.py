@@ -501,6 +501,35 @@ def test_correlation_length_vanishes_for_independent_spins():
     assert np.isnan(xi) or xi < 0.5
 
 
+@pytest.mark.parametrize("L", [4, 8, 12])
+def test_correlation_length_of_plane_defects_closed_form(L):
+    """xi of Sec. 7 from two hand-built lattices measured through the oracle's exchange step
+    (frozen spins, both replicas alike so a swap changes nothing).  A: all up but the plane x = 0;
+    B: all up but the planes x = 0 and y = 0.  With sum_t e^{iKt} = 0 over a period, by hand:
+      A: m = 1 - 2/L, S_x = (-L^2 at t = 0, L^2 else) -> F = |2 L^2|^2 / (3N) = 4L/3;
+      B: m = 1 - 2(2L^2 - L)/N, S_x = S_y = (-L^2 at 0, L^2 - 2L else) -> F = 2 (2L(L-1))^2 / (3N).
+    xi = sqrt(N <m^2> / <F> - 1) over the two measurements: a dropped root, a dropped -1 or a
+    wrong normalisation of F or <m^2> each changes it by far more than the tolerance."""
+    N = L ** 3
+    o = Oracle(L, [1.0, 2.0], field_kind=FIELD_BIMODAL, h=1.0)
+    o.set_measure_xi(True)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    a = np.where(x == 0, -1, 1).astype(np.int8).reshape(-1)
+    b = np.where((x == 0) | (y == 0), -1, 1).astype(np.int8).reshape(-1)
+    for s in (a, b):
+        o.set_spins(np.stack([s, s]))
+        o.exchange(0)
+    assert o.n_meas == 2
+    mA, mB = 1.0 - 2.0 / L, 1.0 - 2.0 * (2 * L * L - L) / N
+    FA, FB = 4.0 * L / 3.0, 2.0 * (2.0 * L * (L - 1)) ** 2 / (3.0 * N)
+    want = math.sqrt(N * (mA ** 2 + mB ** 2) / (FA + FB) - 1.0)
+    th = oracle.thermal(o.observables(), o.observables_F(), o.n_meas, N, o.temps())
+    np.testing.assert_allclose(th[:, 5], 0.5 * (FA + FB), rtol=1e-12)
+    np.testing.assert_allclose(th[:, 3], 0.5 * (mA ** 2 + mB ** 2), rtol=1e-12)
+    np.testing.assert_allclose(th[:, 6], want, rtol=1e-12)
+    assert want > 0.5  # nonzero, so neither the root nor the -1 can be dropped unnoticed
+
+
 # ------------------------------------------------------------------ multi-hit double checkerboard
 @pytest.mark.parametrize("kind", [FIELD_BIMODAL, FIELD_GAUSSIAN])
 def test_multihit_single_site_tiles_single_pass_is_the_plain_checkerboard(kind):

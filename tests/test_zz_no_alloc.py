@@ -39,40 +39,58 @@ def pack_bits(spins: np.ndarray, L: int) -> np.ndarray:
     return out.astype(np.uint32)
 
 
-@pytest.mark.parametrize("L,R,kind", [(16, 8, rf.FIELD_BIMODAL), (64, 16, rf.FIELD_GAUSSIAN),
-                                      (32, 6, rf.FIELD_GAUSSIAN)])
-def test_noalloc_exchange_matches_allocating_entry_point(L, R, kind):
+@pytest.mark.parametrize("L,R,kind,pre,measure_from", [
+    (16, 8, rf.FIELD_BIMODAL, 0, 0),
+    (64, 16, rf.FIELD_GAUSSIAN, 0, 0),
+    (32, 6, rf.FIELD_GAUSSIAN, 0, 0),
+    (8, 4, rf.FIELD_BIMODAL, 0, 0),       # one word per plane: the +-1 neighbour words are the word itself
+    (8, 700, rf.FIELD_GAUSSIAN, 0, 0),    # more replicas than 608: one slab per replica
+    (16, 8, rf.FIELD_BIMODAL, 5, 6),      # permuted start, the first calls before measure_from
+])
+def test_noalloc_exchange_matches_allocating_entry_point(L, R, kind, pre, measure_from):
     temps = inputs.geometric_temps(1.0, 5.0, R)
     h = 1.5 if kind == rf.FIELD_BIMODAL else 1.0
     g = rf.Realization(L, temps, h=h, field_kind=kind, field_seed=3, seed=42, realization=2,
                        layout=rf.LAYOUT_BITPACK)
     g.sweep(7)
+    for _ in range(pre):  # earlier exchange steps of the allocating entry point
+        g.exchange(measure_from)
+        g.sweep(2)
     st = g.get_state()
+    ob0 = g.observables()
+    j0 = int(st["xstep"])
+    assert j0 == pre
     dev = torch.device("cuda")
     spins = torch.from_numpy(pack_bits(st["spins"], L).view(np.int32)).to(dev)
     field = torch.from_numpy(g.field()).to(dev)
     beta = torch.from_numpy(1.0 / temps).to(dev)
-    t2r = torch.arange(R, dtype=torch.int32, device=dev)
-    r2t = torch.arange(R, dtype=torch.int32, device=dev)
-    att = torch.zeros(R - 1, dtype=torch.int64, device=dev)
-    acc = torch.zeros(R - 1, dtype=torch.int64, device=dev)
-    obs = torch.zeros(R, 5, dtype=torch.float64, device=dev)
-    n_meas = torch.zeros(1, dtype=torch.int64, device=dev)
+    t2r_h = st["t2r"].astype(np.int32)
+    r2t_h = np.empty_like(t2r_h)
+    r2t_h[t2r_h] = np.arange(R, dtype=np.int32)
+    if pre:
+        assert not np.array_equal(t2r_h, np.arange(R)), "the start should be a non-identity permutation"
+    t2r = torch.from_numpy(t2r_h).to(dev)
+    r2t = torch.from_numpy(r2t_h).to(dev)
+    att = torch.from_numpy(ob0["att"].astype(np.int64)).to(dev)
+    acc = torch.from_numpy(ob0["acc"].astype(np.int64)).to(dev)
+    obs = torch.from_numpy(np.ascontiguousarray(ob0["sums"], dtype=np.float64)).to(dev)
+    n_meas = torch.tensor([int(ob0["n_meas"])], dtype=torch.int64, device=dev)
     E = torch.zeros(R, dtype=torch.float64, device=dev)
     M = torch.zeros(R, dtype=torch.int64, device=dev)
     b = rf.ExchangeBuffers(L, R, 1.0, h, kind, 42, 2, 0, spins.data_ptr(), field.data_ptr(),
                            beta.data_ptr(), t2r.data_ptr(), r2t.data_ptr(), att.data_ptr(),
                            acc.data_ptr(), obs.data_ptr(), n_meas.data_ptr(), E.data_ptr(), M.data_ptr())
-    for j in range(2):
-        rf.exchange_noalloc(b, j, 0)
-        g.exchange(0)
+    for j in range(j0, j0 + 2):
+        rf.exchange_noalloc(b, j, measure_from)
+        g.exchange(measure_from)
         torch.cuda.synchronize()
         ref = g.get_state(energies=True)
         ob = g.observables()
         np.testing.assert_array_equal(t2r.cpu().numpy(), ref["t2r"])
         np.testing.assert_array_equal(att.cpu().numpy().astype(np.uint64), ob["att"])
         np.testing.assert_array_equal(acc.cpu().numpy().astype(np.uint64), ob["acc"])
-        assert int(n_meas.item()) == ob["n_meas"] == j + 1
+        assert int(n_meas.item()) == ob["n_meas"] == int(ob0["n_meas"]) + sum(
+            1 for k in range(j0, j + 1) if k >= measure_from)
         if kind == rf.FIELD_BIMODAL:
             np.testing.assert_array_equal(E.cpu().numpy(), ref["E"])
             np.testing.assert_array_equal(obs.cpu().numpy(), ob["sums"])
