@@ -8,6 +8,10 @@ runs on the GPU.  Steps continue the same Markov chain.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--layout bitpack|int8]
 
+The JSON line also carries the other spin layout of the same workload (int8 by default) and a
+serving measurement (continuous batching vs per-realization launches on a C5-shaped stream of
+128 realizations x 1000 sweeps, batched kernel tuned first).
+
 Under torchrun each rank runs its own realization (realization id = rank; weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
@@ -35,9 +39,9 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 32 of them per SM per clock on GB300 (measured), which bounds the sweep at 6.4 attempts/clk/SM.
 MULWIDE_PER_CLK_SM = 32.0
 MULWIDE_PER_ATTEMPT = 5.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweeps_bits<64,4,4,float,512> launch (one
-# exchange interval, 3.36e8 attempts) from an ncu capture of this kernel version; None when the
-# kernel changed since (profiles/k_sweeps_bits_L64_R128_gaussian.md).
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
+# (bit layout: one exchange interval, 3.36e8 attempts; int8: one half-sweep, 1.68e7 attempts) from
+# one ncu capture of the current kernel version; None when the kernel changed since the capture.
 SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_halfsweep_int8_rows8": None}
 
 
@@ -51,7 +55,11 @@ def parse():
     p.add_argument("--sweeps", type=int, default=SWEEPS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="c4", choices=["c4", "serve", "adapt", "multihit"])
+    p.add_argument("--workload", default="c4", choices=["c4", "serve", "adapt", "multihit", "profile"])
+    p.add_argument("--profile-case", default="c4", choices=["c4", "c4-bimodal", "c4-int8", "serve", "multihit"])
+    p.add_argument("--no-int8", action="store_true", help="skip the int8-layout sub-measurement")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving sub-measurement")
+    p.add_argument("--serve-realizations", type=int, default=128)
     p.add_argument("--adapt-L", type=int, default=32)
     p.add_argument("--realizations", type=int, default=128)
     p.add_argument("--serve-sweeps", type=int, default=2000)
@@ -220,20 +228,28 @@ def serve_requests(n, sweeps):
     return [(int(L), SERVE_R[int(L)], i) for i, L in enumerate(Ls)], gaps
 
 
-def run_serve(args):
-    """Continuous batching vs plain per-realization launches on the same request stream."""
+def serve_measure(n_real, sweeps, tune=True, with_xi=True):
+    """Continuous batching vs plain per-realization launches on the same C5-shaped request stream
+    (Poisson arrivals at 0.8 x the batched server's closed-loop capacity).  With `tune`, the
+    batched kernel's shapes and intervals per replay come from rfim_server_tune on this mix."""
     import torch
     import paper_1508_06268_gb300 as rf
     from paper_1508_06268_gb300 import inputs
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    reqs, gaps = serve_requests(args.realizations, args.serve_sweeps)
-    ex, sw = EX, args.serve_sweeps
+    reqs, gaps = serve_requests(n_real, sweeps)
+    ex, sw = EX, sweeps
     mf = sw // ex // 2
     temps = {L: inputs.geometric_temps(T_MIN, T_MAX, R_) for L, R_ in SERVE_R.items()}
     work = sum(L ** 3 * R_ * sw for L, R_, _ in reqs)
+    tuned = None
+    if tune:
+        t0 = time.perf_counter()
+        tuned = rf.server_tune(sorted(SERVE_R.items()), field_kind=rf.FIELD_GAUSSIAN, sweeps=200, exchange_every=ex)
+        tuned["seconds"] = round(time.perf_counter() - t0, 2)
 
     def batched(arrivals, xi=False):
-        srv = rf.Server(mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4, measure_xi=xi)
+        # intervals_per_launch 0 and no explicit shapes: the tuned settings (built-in ones untuned)
+        srv = rf.Server(mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=0 if tune else 4,
+                        measure_xi=xi)
         t0 = time.perf_counter()
         pend, lat, i = {}, [], 0
         while len(lat) < len(reqs):
@@ -271,27 +287,69 @@ def run_serve(args):
     # warm-up (module load, graph capture), then the closed-loop capacity of the batched server
     batched(np.zeros(len(reqs)))
     _, span_closed, _ = batched(np.zeros(len(reqs)))
-    # the same with the structure factor of the correlation length measured in the batched kernel
-    _, span_closed_xi, _ = batched(np.zeros(len(reqs)), xi=True)
+    span_closed_xi = None
+    if with_xi:  # the same with the structure factor of the correlation length in the batched kernel
+        _, span_closed_xi, _ = batched(np.zeros(len(reqs)), xi=True)
     rate = 0.8 * len(reqs) / span_closed  # realizations / s offered to both servers
     arrivals = np.cumsum(gaps) / rate
     arrivals -= arrivals[0]
     lat_b, span_b, st = batched(arrivals)
     lat_s, span_s = sequential(arrivals)
-    line = {
+    torch.cuda.synchronize()
+    return {
         "metric": "served realizations: p50/p99 latency and spin-flip attempts/ns (batched vs per-realization)",
         "workload": "C5-shaped: Gaussian h=1, L uniform in {8,16,32,64}, R=16/32/64/128",
         "realizations": len(reqs), "sweeps_each": sw, "exchange_every": ex,
         "offered_rate_per_s": rate, "arrivals": "Poisson (seed 2024), 0.8 x closed-loop batched capacity",
+        "tuned": tuned,
         "batched": {"p50_s": float(np.percentile(lat_b, 50)), "p99_s": float(np.percentile(lat_b, 99)),
                     "attempts_per_ns": work / (span_b * 1e9), "makespan_s": span_b,
                     "closed_loop_attempts_per_ns": work / (span_closed * 1e9),
-                    "closed_loop_xi_attempts_per_ns": work / (span_closed_xi * 1e9),
-                    "graph_launches": st["graph_launches"], "grid": st["grid"]},
+                    "closed_loop_xi_attempts_per_ns": None if span_closed_xi is None
+                    else work / (span_closed_xi * 1e9),
+                    "graph_launches": st["graph_launches"], "grid": st["grid"],
+                    "batch_shapes": st["batch_shapes"], "intervals_per_launch": st["intervals_per_launch"]},
         "per_realization": {"p50_s": float(np.percentile(lat_s, 50)), "p99_s": float(np.percentile(lat_s, 99)),
                             "attempts_per_ns": work / (span_s * 1e9), "makespan_s": span_s},
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps(serve_measure(args.realizations, args.serve_sweeps)), flush=True)
+
+
+def run_profile(args):
+    """Small fixed workloads for ncu captures of one kernel (commands in profiles/): the C4 shape
+    (L = 64, R = 128, four exchange intervals of 10 sweeps; Gaussian, bimodal or int8 layout), the
+    batched serving kernel on 16 C5-shaped Gaussian realizations of 400 sweeps submitted at once,
+    or multi-hit sweeps (mh = 100, tiles 8^3, four launches of one sweep)."""
+    import torch
+    import paper_1508_06268_gb300 as rf
+    from paper_1508_06268_gb300 import inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    case = args.profile_case
+    if case == "serve":
+        with rf.Server(mem_budget_bytes=2 << 30, max_slots=64, intervals_per_launch=4) as srv:
+            tickets = [srv.submit(L_, inputs.geometric_temps(T_MIN, T_MAX, R_), 400, EX, 20,
+                                  field_kind=rf.FIELD_GAUSSIAN, field_seed=1 + k, realization=k)
+                       for k, (L_, R_) in enumerate(sorted(SERVE_R.items()) * 4)]
+            for t in tickets:
+                srv.wait(t)
+        print("ok", len(tickets))
+    elif case == "multihit":
+        g = rf.Realization(L, inputs.geometric_temps(T_MIN, T_MAX, R), field_kind=rf.FIELD_GAUSSIAN)
+        g.set_multihit(100, 8)
+        g.run(4, 1, 0)
+        print("ok", g.get_state(spins=False)["sweep"])
+    else:
+        layout = rf.LAYOUT_INT8 if case == "c4-int8" else rf.LAYOUT_BITPACK
+        kind = rf.FIELD_BIMODAL if case == "c4-bimodal" else rf.FIELD_GAUSSIAN
+        g = rf.Realization(L, inputs.geometric_temps(T_MIN, T_MAX, R), field_kind=kind, layout=layout)
+        g.run(40, EX, 0)
+        print("ok", g.get_state(spins=False)["sweep"])
+    torch.cuda.synchronize()
 
 
 # Sec. 4 and the comparison of adaptive and homogeneous temperature sets (Table 1, the exchange-rate
@@ -423,39 +481,10 @@ def run_int_rates():
         subprocess.run([exe], check=True)
 
 
-def main():
-    args = parse()
-    if args.int_rates:
-        run_int_rates()
-        return
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.workload == "serve":
-        run_serve(args)
-        return
-    if args.workload == "adapt":
-        run_adapt(args)
-        return
-    if args.workload == "multihit":
-        run_multihit(args)
-        return
-    import torch
-    import paper_1508_06268_gb300 as rf
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    layout = rf.LAYOUT_BITPACK if args.layout == "bitpack" else rf.LAYOUT_INT8
-    T = temps()
-    sh = shard_for_rank(rank)
-    real = sh["realization"]
-    g = rf.Realization(L, T, J=J, h=H, field_kind=rf.FIELD_GAUSSIAN, field_seed=sh["field_seed"], seed=42,
+def measure_layout(rf, torch, layout, args, T, real, field_seed, local, dist):
+    """W untimed steps, then K timed steps (L2 flushed before each) of the C4 workload in one
+    layout; returns the device time (max over ranks), wall time, kernel profile, launches, clocks."""
+    g = rf.Realization(L, T, J=J, h=H, field_kind=rf.FIELD_GAUSSIAN, field_seed=field_seed, seed=42,
                        realization=real, layout=layout)
     stream = torch.cuda.current_stream()
     measure_from = args.sweeps // EX // 2
@@ -486,33 +515,90 @@ def main():
     prof = g.profile_read()
     g.profile(False)
     launches = g.launch_count - launches0
+    g.close()
+    del flush
     if dist is not None:
         dist.barrier()
-    dev_ms_max = max_over_ranks(dev_ms, dist, "cuda")
-    attempts_rank = L ** 3 * R * args.sweeps * args.steps
-    value = aggregate_rate(attempts_rank, world, dev_ms_max)
+    return {"dev_ms": max_over_ranks(dev_ms, dist, "cuda"), "dev_ms_local": dev_ms, "wall": wall, "prof": prof,
+            "launches": launches, "clk": clk}
 
-    # dominant kernel: the sweep kernel (one launch per exchange interval)
-    sweep_launch_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
-    attempts_per_launch = L ** 3 * R * EX
-    achieved = attempts_per_launch / (sweep_launch_ms * 1e6)  # Gattempts/s
-    props = torch.cuda.get_device_properties(local)
+
+def roofline_of(m, layout, rf, props, steps):
+    """Dominant kernel of the layout against the Philox integer roof at the sampled SM clock:
+    attempts of one launch group (one exchange interval of EX sweeps) / its CUDA-event time."""
+    prof, clk = m["prof"], m["clk"]
+    group_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
+    achieved = L ** 3 * R * EX / (group_ms * 1e6)  # Gattempts/s
     sm_mhz = clk["sm_mhz"] or 2070.0
     peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s",
-                "frac": achieved / peak,
-                "traffic": SWEEP_TRAFFIC_BYTES.get("k_sweeps_bits") if layout == rf.LAYOUT_BITPACK else None,
-                "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
-                "kernel": "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8_rows8",
-                "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
-                              f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
-                              f"{sm_mhz:.0f} MHz (median sampled)",
-                "sweep_kernel_share": prof["sweep_ms"] / max(dev_ms, 1e-9),
-                "exchange_ms_per_step": prof["exchange_ms"] / args.steps}
+    kernel = "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8_rows8"
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s", "frac": achieved / peak,
+            "traffic": SWEEP_TRAFFIC_BYTES.get(kernel), "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
+            "kernel": kernel,
+            "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
+                          f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
+                          f"{sm_mhz:.0f} MHz (median sampled)",
+            "sweep_kernel_share": prof["sweep_ms"] / max(m["dev_ms_local"], 1e-9),
+            "exchange_ms_per_step": prof["exchange_ms"] / steps}
+
+
+def main():
+    args = parse()
+    if args.int_rates:
+        run_int_rates()
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
+        return
+    if args.workload == "adapt":
+        run_adapt(args)
+        return
+    if args.workload == "multihit":
+        run_multihit(args)
+        return
+    if args.workload == "profile":
+        run_profile(args)
+        return
+    import torch
+    import paper_1508_06268_gb300 as rf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    layout = rf.LAYOUT_BITPACK if args.layout == "bitpack" else rf.LAYOUT_INT8
+    T = temps()
+    sh = shard_for_rank(rank)
+    real = sh["realization"]
+    props = torch.cuda.get_device_properties(local)
+    m = measure_layout(rf, torch, layout, args, T, real, sh["field_seed"], local, dist)
+    attempts_rank = L ** 3 * R * args.sweeps * args.steps
+    value = aggregate_rate(attempts_rank, world, m["dev_ms"])
+    roofline = roofline_of(m, layout, rf, props, args.steps)
+
+    # the other spin layout of the C4 workload (the headline is the bit layout by default)
+    other = None
+    if not args.no_int8:
+        olay = rf.LAYOUT_INT8 if layout == rf.LAYOUT_BITPACK else rf.LAYOUT_BITPACK
+        mo = measure_layout(rf, torch, olay, args, T, real, sh["field_seed"], local, dist)
+        other = {"layout": "int8" if olay == rf.LAYOUT_INT8 else "bitpack",
+                 "value": aggregate_rate(attempts_rank, world, mo["dev_ms"]), "unit": "attempts/ns",
+                 "ms_per_step": mo["dev_ms"] / args.steps, "gpu_launches": mo["launches"],
+                 "roofline": roofline_of(mo, olay, rf, props, args.steps), "clocks": mo["clk"]}
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(rf, torch, T, layout, args, real)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = serve_measure(args.serve_realizations, 1000, tune=True, with_xi=False)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -520,16 +606,18 @@ def main():
         line = {
             "metric": "spin-flip attempts/ns at L=64", "value": value, "unit": "attempts/ns",
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
-            "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": m["dev_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
             "config": {"workload": "C4: L=64 (262144 sites) Gaussian h=1, J=1, R=128 geometric [1,5], "
                                    f"{args.sweeps} sweeps/step, exchange every {EX}",
                        "layout": args.layout, "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"realization per GPU x{world}",
-                       "wall_s": wall},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk,
+                       "wall_s": m["wall"]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches"],
+            "clocks": m["clk"], "serving": serving,
         }
+        if other is not None:  # the second layout of the C4 workload under its own name
+            line[other["layout"]] = other
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

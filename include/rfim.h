@@ -54,6 +54,7 @@ extern "C" {
 #define RFIM_ETIMEOUT (-4) /* a bounded device-side wait expired */
 #define RFIM_EBUSY (-5)    /* result not ready yet (serving poll) */
 #define RFIM_ESTATE (-6)   /* call not valid in the current state */
+#define RFIM_EBOUNDS (-7)  /* a device bounds check failed (debug build librfim_debug.so only) */
 
 /* field kinds (Sec. 3.1 step 2 uses the bimodal field) */
 #define RFIM_FIELD_BIMODAL 0  /* h_i = +-1 equiprobable, drawn from field_seed */
@@ -209,15 +210,21 @@ typedef struct rfim_server rfim_server;
 typedef struct {
   uint64_t mem_budget_bytes;    /* device arena for resident realizations (admission control) */
   int32_t max_slots;            /* realizations resident at the same time, >= 1 */
-  int32_t intervals_per_launch; /* exchange intervals per graph replay, >= 1 */
+  int32_t intervals_per_launch; /* exchange intervals per graph replay, >= 1; 0: the value chosen by
+                                   the last rfim_server_tune of this process, else 4 */
   int32_t measure_xi;           /* != 0: also accumulate the structure factor F (rfim_set_measure_xi)
                                    on every measuring exchange step, fused into the batched kernel */
+  const char *batch_shapes;     /* "L:G:GT,...": replicas per work item G and per thread GT of the
+                                   batched kernel for each listed L (copied); NULL: the shapes of
+                                   the last rfim_server_tune of this process, else built-in ones */
 } rfim_server_config;
 typedef struct {
   int64_t queued, resident, completed, graph_launches;
   double busy_s;   /* seconds spent in graph replays */
   double attempts; /* spin-flip attempts of completed realizations */
   int32_t grid;    /* CTAs of the persistent batched kernel */
+  int32_t intervals_per_launch;
+  char batch_shapes[64]; /* the shapes in use, "L:G:GT,..." for L = 64, 32, 16, 8 */
 } rfim_server_info;
 /* Errors: RFIM_EINVAL (bad configuration), RFIM_ENOMEM (arena), RFIM_ECUDA. */
 int rfim_server_create(const rfim_server_config *cfg, rfim_server **out);
@@ -234,6 +241,29 @@ int rfim_server_poll(rfim_server *s, uint64_t ticket, rfim_obs *out, double *lat
 int rfim_server_stats(rfim_server *s, rfim_server_info *out);
 /* Stops the worker (resident work is abandoned) and frees everything.  NULL is accepted. */
 int rfim_server_destroy(rfim_server *s);
+/* Tuner of the batched kernel (spec batching pattern; it stands in for the paper's choice
+   of block shape by the cost model of Sec. 3.2, Eq. (S) and (dS), which is prior art for Kepler).
+   For each L of the expected mix it times every instantiated (G, GT) shape -- replicas per work
+   item and per thread -- on scratch realizations of that L (enough to fill the GPU twice,
+   sweeps each, closed loop on a scratch server with the other L at their best shapes so far),
+   then times intervals_per_launch in {1, 2, 4, 8} on the whole mix with the chosen shapes.
+   Later rfim_server_create calls in this process with batch_shapes == NULL and
+   intervals_per_launch == 0 use the result.  Shapes and intervals change the launch only, not
+   the results: every served realization takes the same decisions and sums in the same order
+   whatever they are.  shapes_out (optional, cap chars) receives "L:G:GT,...", *intervals_out
+   (optional) the interval count, *attempts_per_ns (optional) the rate of the chosen setting.
+   Synchronous; creates scratch servers of mem_budget_bytes.  Errors: RFIM_EINVAL, RFIM_ENOMEM,
+   RFIM_ECUDA (message in rfim_server_last_error(NULL)). */
+typedef struct {
+  int32_t n;                 /* entries of the expected mix */
+  const int32_t *L, *R;      /* their lattice sizes (8, 16, 32, 64) and replica counts (<= 1024) */
+  int32_t field_kind;        /* RFIM_FIELD_BIMODAL or RFIM_FIELD_GAUSSIAN (seeded scratch fields) */
+  int32_t exchange_every;
+  int64_t sweeps;            /* per scratch realization, a positive multiple of exchange_every */
+  uint64_t mem_budget_bytes; /* arena of each scratch server */
+} rfim_server_tune_config;
+int rfim_server_tune(const rfim_server_tune_config *t, char *shapes_out, int32_t cap, int32_t *intervals_out,
+                     double *attempts_per_ns);
 const char *rfim_server_last_error(const rfim_server *s);
 
 /* ---- Exchange step without device allocation ------------------------------------------------------
@@ -313,6 +343,22 @@ int rfim_selftest_grid(int32_t L, int32_t R, int32_t P);
    was seen, RFIM_EINVAL for a bad spin_limit, RFIM_ECUDA on a CUDA error.  Synchronous on the
    default stream; the context of the calling thread stays usable after an expiry. */
 int rfim_selftest_wait(int32_t spin_limit, int32_t set_flag);
+
+/* Bounds-checked build (no counterpart in the paper; it stands in for a memory checker).  The same
+   sources compiled with -DRFIM_DEBUG give librfim_debug.so (same C ABI; the Python binding loads it
+   when RFIM_LIBRARY=debug).  In it the sweep kernels check the shared-memory lattice indices, the
+   decision-table slots against the dynamic shared memory, the cluster peer ranks of the halo
+   loads, the grid-wide partition (pieces, planes, owners, partial slots) and the no-alloc scratch
+   slots; a failed check sets a bit of the launch's device error word and the access is skipped or
+   redirected to a harmless index, so the kernel still ends normally (nothing traps).  The word is
+   reported as RFIM_EBOUNDS by rfim_observables / rfim_get_state, by the server (fatal, at the next
+   poll) and, after a synchronisation, by rfim_exchange_noalloc.  rfim_debug_build returns 1 in
+   that library and 0 in librfim.so.  rfim_selftest_debug (debug library only; RFIM_ESTATE
+   otherwise) runs one checked index that is out of range on purpose and returns RFIM_OK when the
+   check caught it and the kernel finished, RFIM_EBOUNDS if it was not caught, RFIM_ECUDA on a CUDA
+   error.  Synchronous on the default stream. */
+int rfim_debug_build(void);
+int rfim_selftest_debug(void);
 
 #ifdef __cplusplus
 }

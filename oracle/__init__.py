@@ -5,8 +5,9 @@ import this package.  It wraps ``rfim_oracle.c`` (plain single-threaded C, no fu
 through ctypes and shares nothing with the CUDA path.  The C source cites the paper's sections
 and equations it follows; the random-number contract is stated in its header comment.
 
-Functions without an independent pin are listed in the repository's design notes; every
-function here is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
+Every function here is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``
+against facts that do not come from the oracle itself (brute force, exact enumeration, closed
+forms, an independent Philox implementation, numpy FFTs).
 """
 from __future__ import annotations
 

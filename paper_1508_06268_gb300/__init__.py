@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _build
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ESTATE, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 FIELD_BIMODAL, FIELD_GAUSSIAN, FIELD_EXPLICIT = 0, 1, 2
 LAYOUT_INT8, LAYOUT_BITPACK = 0, 1
 
@@ -54,27 +54,39 @@ class ExchangeBuffers(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32),
-                ("intervals_per_launch", C.c_int32), ("measure_xi", C.c_int32)]
+                ("intervals_per_launch", C.c_int32), ("measure_xi", C.c_int32),
+                ("batch_shapes", C.c_char_p)]
 
 
 class ServerInfo(C.Structure):
     _fields_ = [("queued", C.c_int64), ("resident", C.c_int64), ("completed", C.c_int64),
                 ("graph_launches", C.c_int64), ("busy_s", C.c_double), ("attempts", C.c_double),
-                ("grid", C.c_int32)]
+                ("grid", C.c_int32), ("intervals_per_launch", C.c_int32), ("batch_shapes", C.c_char * 64)]
+
+
+class ServerTuneConfig(C.Structure):
+    _fields_ = [("n", C.c_int32), ("L", C.c_void_p), ("R", C.c_void_p), ("field_kind", C.c_int32),
+                ("exchange_every", C.c_int32), ("sweeps", C.c_int64), ("mem_budget_bytes", C.c_uint64)]
+
+
+def debug_flavour() -> bool:
+    """RFIM_LIBRARY=debug selects the bounds-checked build librfim_debug.so (same C ABI)."""
+    return os.environ.get("RFIM_LIBRARY", "") == "debug"
 
 
 def lib_path() -> str:
-    return _build.LIB
+    return _build.lib_path(debug_flavour())
 
 
 def load():
-    """Loads librfim.so, building it first if it is missing or stale."""
+    """Loads librfim.so (librfim_debug.so with RFIM_LIBRARY=debug), building it first if it is
+    missing or stale."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=debug_flavour())
             if not os.path.exists(path):
-                raise RuntimeError("librfim.so is missing and could not be built")
+                raise RuntimeError(f"{os.path.basename(path)} is missing and could not be built")
             L = C.CDLL(path)
             P, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
             L.rfim_create.argtypes = [C.POINTER(Config), C.POINTER(C.c_void_p)]
@@ -102,11 +114,15 @@ def load():
             L.rfim_exchange_noalloc.argtypes = [C.POINTER(ExchangeBuffers), u32, i64, P]
             L.rfim_selftest_grid.argtypes = [i32, i32, i32]
             L.rfim_selftest_wait.argtypes = [i32, i32]
+            L.rfim_debug_build.argtypes = []
+            L.rfim_selftest_debug.argtypes = []
             L.rfim_set_measure_xi.argtypes = [P, i32]
             L.rfim_set_multihit.argtypes = [P, i32, i32]
             L.rfim_thermal.argtypes = [C.POINTER(Obs), i32, P]
             L.rfim_disorder_average.argtypes = [P, i32, i32, P]
             L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
+            L.rfim_server_tune.argtypes = [C.POINTER(ServerTuneConfig), C.c_char_p, i32, C.POINTER(i32),
+                                           C.POINTER(C.c_double)]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
             for name in ("rfim_create", "rfim_destroy", "rfim_sweep", "rfim_exchange", "rfim_run",
@@ -116,7 +132,8 @@ def load():
                          "rfim_server_poll", "rfim_server_stats", "rfim_server_destroy",
                          "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid", "rfim_selftest_wait",
                          "rfim_set_measure_xi", "rfim_set_multihit", "rfim_thermal",
-                         "rfim_disorder_average"):
+                         "rfim_disorder_average", "rfim_server_tune", "rfim_debug_build",
+                         "rfim_selftest_debug"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -149,6 +166,35 @@ def tune(L: int, R: int, field_kind: int = FIELD_GAUSSIAN):
     if rc != OK:
         raise RfimError(rc, lib.rfim_last_error(None).decode())
     return buf.value.decode(), rate.value
+
+
+def server_tune(mix, field_kind: int = FIELD_GAUSSIAN, sweeps: int = 200, exchange_every: int = 10,
+                mem_budget_bytes: int = 4 << 30):
+    """Runs the batched-kernel tuner (rfim_server_tune) on an expected mix of (L, R) pairs; returns
+    {"batch_shapes": "L:G:GT,...", "intervals_per_launch": K, "attempts_per_ns": rate}.  Servers
+    created later with the defaults use the result."""
+    lib = load()
+    Ls = np.ascontiguousarray([m[0] for m in mix], dtype=np.int32)
+    Rs = np.ascontiguousarray([m[1] for m in mix], dtype=np.int32)
+    cfg = ServerTuneConfig(len(Ls), Ls.ctypes.data, Rs.ctypes.data, field_kind, exchange_every, sweeps,
+                           mem_budget_bytes)
+    buf = C.create_string_buffer(64)
+    k = C.c_int32()
+    rate = C.c_double()
+    rc = lib.rfim_server_tune(C.byref(cfg), buf, 64, C.byref(k), C.byref(rate))
+    if rc != OK:
+        raise RfimError(rc, lib.rfim_server_last_error(None).decode())
+    return {"batch_shapes": buf.value.decode(), "intervals_per_launch": k.value, "attempts_per_ns": rate.value}
+
+
+def debug_build() -> bool:
+    """True when the loaded library is the bounds-checked flavour."""
+    return bool(load().rfim_debug_build())
+
+
+def selftest_debug() -> int:
+    """rfim_selftest_debug: OK when a deliberately out-of-range checked index was caught."""
+    return load().rfim_selftest_debug()
 
 
 def selftest_grid(L: int, R: int, P: int) -> int:
@@ -335,10 +381,14 @@ class Realization:
 class Server:
     """Continuous-batching server of independent realizations (include/rfim.h, serving section)."""
 
-    def __init__(self, mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4, measure_xi=False):
+    def __init__(self, mem_budget_bytes=4 << 30, max_slots=256, intervals_per_launch=4, measure_xi=False,
+                 batch_shapes=None):
+        """intervals_per_launch = 0 and batch_shapes = None take the last server_tune result of this
+        process (else the built-in settings); batch_shapes is "L:G:GT,..." to fix them."""
         self._lib = load()
         self._h = None
-        cfg = ServerConfig(mem_budget_bytes, max_slots, intervals_per_launch, 1 if measure_xi else 0)
+        self._shapes = None if batch_shapes is None else batch_shapes.encode()
+        cfg = ServerConfig(mem_budget_bytes, max_slots, intervals_per_launch, 1 if measure_xi else 0, self._shapes)
         out = C.c_void_p()
         rc = self._lib.rfim_server_create(C.byref(cfg), C.byref(out))
         if rc != OK:
@@ -425,4 +475,6 @@ class Server:
         rc = self._lib.rfim_server_stats(self._h, C.byref(info))
         if rc != OK:
             raise self._err(rc)
-        return {k: getattr(info, k) for k, _ in ServerInfo._fields_}
+        out = {k: getattr(info, k) for k, _ in ServerInfo._fields_}
+        out["batch_shapes"] = info.batch_shapes.decode()
+        return out

@@ -14,6 +14,7 @@
 
 #include "rfim.h"
 #include "bits_layout.cuh"
+#include "debug_check.cuh"
 #include "exchange.cuh"
 #include "internal.h"
 #include "lattice.cuh"
@@ -58,6 +59,10 @@ __global__ void __launch_bounds__(256) k_exchange_noalloc(NoAllocArgs a, uint32_
   long long *partFi = partM + kNoAllocSlots;
   double *partF = reinterpret_cast<double *>(partFi + kNoAllocSlots);
   unsigned int *counter = reinterpret_cast<unsigned int *>(scratch + kCounterOffset);
+  // debug build: this CTA's partial slot must lie inside the static array (else it writes none)
+  const bool slot_ok = RFIM_DCHECK(counter + 1, blockIdx.x < (unsigned)kNoAllocSlots && gridDim.x <= (unsigned)kNoAllocSlots &&
+                                                    (int)blockIdx.x / a.slabs < v.R,
+                                   kDbgScratch);
   const int r = blockIdx.x / a.slabs, slab = blockIdx.x % a.slabs;
   const int z0 = (int)((int64_t)slab * L / a.slabs), z1 = (int)((int64_t)(slab + 1) * L / a.slabs);
   const uint32_t *S0 = v.bits + (int64_t)r * 2 * W, *S1 = S0 + W;
@@ -118,10 +123,12 @@ __global__ void __launch_bounds__(256) k_exchange_noalloc(NoAllocArgs a, uint32_
       tf += si[2][w];
       td += sd[w];
     }
-    partB[blockIdx.x] = tb;
-    partM[blockIdx.x] = tm;
-    partFi[blockIdx.x] = tf;
-    partF[blockIdx.x] = td;
+    if (slot_ok) {
+      partB[blockIdx.x] = tb;
+      partM[blockIdx.x] = tm;
+      partFi[blockIdx.x] = tf;
+      partF[blockIdx.x] = td;
+    }
     __threadfence();
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
@@ -209,5 +216,16 @@ extern "C" int rfim_exchange_noalloc(const rfim_exchange_buffers *b, uint32_t j,
   e = cudaGetLastError();
   if (e != cudaSuccess)
     return set_thread_error(RFIM_ECUDA, std::string("rfim_exchange_noalloc: launch: ") + cudaGetErrorString(e));
+  if (kDebugBuild) {  // debug build only: wait for the launch and report its bounds checks
+    unsigned int word = 0, zero = 0;
+    unsigned int *err = reinterpret_cast<unsigned int *>(scratch + kCounterOffset) + 1;
+    e = cudaMemcpyAsync(&word, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && word) e = cudaMemcpyAsync(err, &zero, 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      return set_thread_error(RFIM_ECUDA, std::string("rfim_exchange_noalloc: ") + cudaGetErrorString(e));
+    if (word) return set_thread_error(RFIM_EBOUNDS, "rfim_exchange_noalloc: a bounds check of the debug build failed");
+  }
   return RFIM_OK;
 }

@@ -515,6 +515,41 @@ extern "C" int rfim_selftest_wait(int32_t spin_limit, int32_t set_flag) {
   return h[1] ? -4 : 0;             // RFIM_ETIMEOUT : RFIM_OK
 }
 
+// Debug-build self-check of the check mechanism: a checked shared-memory index out of range is
+// recorded in the error word and replaced by index 0, and the kernel finishes normally.
+namespace {
+__global__ void k_selftest_debug(unsigned *words, int index) {
+  __shared__ unsigned cells[32];
+  if (threadIdx.x < 32) cells[threadIdx.x] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int i = index;
+    if (!RFIM_DCHECK(words + 1, i >= 0 && i < 32, rfim::kDbgLattice)) i = 0;
+    cells[i] = 7u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) words[0] = cells[0];
+}
+}  // namespace
+
+extern "C" int rfim_debug_build(void) { return rfim::kDebugBuild ? 1 : 0; }
+
+extern "C" int rfim_selftest_debug(void) {
+  if (!rfim::kDebugBuild) return -6;  // RFIM_ESTATE: the checks are compiled only into librfim_debug.so
+  unsigned *d = nullptr;
+  unsigned h[2] = {0u, 0u};
+  if (cudaMalloc(&d, sizeof h) != cudaSuccess) return -3;
+  cudaError_t e = cudaMemcpy(d, h, sizeof h, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_selftest_debug<<<1, 32>>>(d, 40);  // out of range on purpose: the check must catch it
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return -3;
+  return (h[0] == 7u && h[1] == rfim::kDbgLattice) ? 0 : -7;  // RFIM_OK : RFIM_EBOUNDS (not caught)
+}
+
 extern "C" int rfim_selftest_grid(int32_t L, int32_t R, int32_t P) {
   using namespace rfim;
   if (L < 2 || R < 2 || P < 1) return -1;

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "bits_layout.cuh"
+#include "debug_check.cuh"
 #include "decide.cuh"
 #include "exchange.cuh"
 #include "internal.h"
@@ -564,11 +565,19 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
   const uint32_t slot0 = tab_slot0(tab);
   const int nt = blockDim.x, tid = threadIdx.x;
 
-  for (int t = tid; t < gact * 2 * WC; t += nt) {
+  // debug build: the replica range, the decision-table slots and the cluster peers must lie
+  // inside the realization, the dynamic shared memory and the cluster; otherwise nothing is
+  // updated (every thread agrees, so the barriers still match)
+  const bool ok = RFIM_DCHECK(xa.err, gact >= 1 && gact <= G && r0 >= 0 && r0 + gact <= v.R, kDbgGlobal) &&
+                  RFIM_DCHECK(xa.err, slot0 + (uint32_t)gact * kTabSlot <= (uint32_t)__cvta_generic_to_shared(sm) + dyn_smem_bytes() &&
+                                          (uint32_t)__cvta_generic_to_shared(tab) + kTabSlot - 1u >= slot0,
+                              kDbgTable) &&
+                  RFIM_DCHECK(xa.err, S == 1 || (cluster_ctas() == (uint32_t)S && up_rank < S && dn_rank < S), kDbgRank);
+  for (int t = tid; ok && t < gact * 2 * WC; t += nt) {
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     sp[t] = v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl];
   }
-  tab_fill<BIM>(v, tab, slot0, gact, [&](int g) { return r0 + g; });
+  if (ok) tab_fill<BIM>(v, tab, slot0, gact, [&](int g) { return r0 + g; });
   sync_slabs<S>();
 
   const int ngroups = (gact + GT - 1) / GT;
@@ -582,10 +591,11 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
       // multi-hit kernel uses): the call changes the register allocation of this kernel (100 ->
       // 128 registers with spills for the float field at L = 64)
 #pragma unroll 1
-      for (int item = tid; item < items; item += nt) {
+      for (int item = tid; ok && item < items; item += nt) {
         const int wl = item % WC, grp = item / WC;
         const int zl = wl / P, iw = wl % P;
         const int z = z0 + zl;
+        if (!RFIM_DCHECK(xa.err, grp * GT < gact && zl < PZ && iw < P, kDbgLattice)) continue;
         const int64_t wq = (int64_t)z * P + iw;
         float4 hh4[8] = {};
         if (!BIM) {
@@ -639,11 +649,11 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
     }
   }
 
-  for (int t = tid; t < gact * 2 * WC; t += nt) {
+  for (int t = tid; ok && t < gact * 2 * WC; t += nt) {
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
     v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl] = sp[t];
   }
-  if (xa.enabled) interval_tail<L, S, BIM, XI>(v, G, r0, gact, rank, nsw, field4, xa);
+  if (xa.enabled) interval_tail<L, S, BIM, XI>(v, G, r0, ok ? gact : 0, rank, nsw, field4, xa);
 }
 
 template <int L, int S, int GT, bool BIM, int NT>

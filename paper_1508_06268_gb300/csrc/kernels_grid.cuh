@@ -87,7 +87,11 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     nb_s = nend;
   }
   __syncthreads();
-  const int np = np_s, nu = nu_s, nb = nb_s;
+  // debug build: the partition must fit the shared-memory plan (pieces, planes, local order)
+  const bool part_ok = RFIM_DCHECK(xa.err, np_s >= 1 && np_s <= kGridMaxPieces && nu_s <= ga.max_units && nu_s <= 255 &&
+                                               nb_s <= nu_s,
+                                   kDbgPartition);
+  const int np = part_ok ? np_s : 0, nu = part_ok ? nu_s : 0, nb = part_ok ? nb_s : 0;
   uint32_t *lat = sm;                                          // [max_units][GG][2][PW]
   uint32_t *halo = lat + (size_t)ga.max_units * GG * 2 * PW;  // [pieces][2][GG][PW] (other colour)
   uint32_t *tab = halo + (size_t)kGridMaxPieces * 2 * GG * PW;  // [pieces][GG] decision-table slots
@@ -123,8 +127,9 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     if (lt == 0) {
       for (int p = 0; p < np; ++p) {
         const int64_t base = (int64_t)pc[p].g * L;
-        const int klo = grid_owner(ga.gp, base + (pc[p].z0 + L - 1) % L);
-        const int khi = grid_owner(ga.gp, base + (pc[p].z0 + pc[p].n) % L);
+        int klo = grid_owner(ga.gp, base + (pc[p].z0 + L - 1) % L);
+        int khi = grid_owner(ga.gp, base + (pc[p].z0 + pc[p].n) % L);
+        if (!RFIM_DCHECK(err, klo >= 0 && klo < ga.gp.P && khi >= 0 && khi < ga.gp.P, kDbgPartition)) klo = khi = k;
         grid_wait(ga.prog, klo, need, err);
         grid_wait(ga.prog, khi, need, err);
       }
@@ -160,6 +165,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
         const bool end_plane = it < nb * IPW;
         const int gb = (it % IPW) / PW * GTI;  // first replica of this item within the group
         const int p = plane_piece[lu];
+        if (!RFIM_DCHECK(err, lu < nu && p >= 0 && p < np && pc[p].z0 + (lu - pc[p].lu0) < L, kDbgPartition)) continue;
         const int z = pc[p].z0 + (lu - pc[p].lu0);
         const int64_t wq = (int64_t)z * PW + w;
         const int gact = gact_of(p);
@@ -300,11 +306,14 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
           tf += red_i[2][w];
           td += red_d[w];
         }
-        const int64_t slot = (int64_t)(pc[p].g * GG + gg) * ga.slots + grid_slab_of(ga.gp, k, pc[p].g);
-        ga.partB[slot] = tb;
-        ga.partM[slot] = tm;
-        ga.partFi[slot] = tf;
-        ga.partF[slot] = td;
+        const int slab = grid_slab_of(ga.gp, k, pc[p].g);
+        const int64_t slot = (int64_t)(pc[p].g * GG + gg) * ga.slots + slab;
+        if (RFIM_DCHECK(xa.err, slab >= 0 && slab < ga.slots && pc[p].g * GG + gg < v.R, kDbgPartition)) {
+          ga.partB[slot] = tb;
+          ga.partM[slot] = tm;
+          ga.partFi[slot] = tf;
+          ga.partF[slot] = td;
+        }
       }
       __syncthreads();
     }

@@ -14,6 +14,7 @@
 #include "rfim.h"
 #include "internal.h"
 #include "sweep_bits.h"
+#include "debug_check.cuh"
 
 using namespace rfim;
 
@@ -194,8 +195,9 @@ int reset_state(rfim_ctx *c, uint32_t stage) {
   return RFIM_OK;
 }
 
-// Bounded device waits that expired (bit-layout kernels) surface as RFIM_ETIMEOUT; the word is
-// cleared once reported.  Synchronises the stream.
+// Bounded device waits that expired (bit-layout kernels) surface as RFIM_ETIMEOUT, failed bounds
+// checks of the debug build as RFIM_EBOUNDS; the word is cleared once reported.  Synchronises the
+// stream.
 int check_device_error(rfim_ctx *c) {
   if (c->layout != RFIM_LAYOUT_BITPACK || !c->plan.counter) return RFIM_OK;
   unsigned int word = 0;
@@ -203,6 +205,8 @@ int check_device_error(rfim_ctx *c) {
   CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
   if (!word) return RFIM_OK;
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.counter + 1, 0, 4, c->stream));
+  if (word & kDbgMask)
+    return fail(c, RFIM_EBOUNDS, "a bounds check of the debug build failed (error word 0x%x); the checked accesses were skipped", word);
   return fail(c, RFIM_ETIMEOUT, "a bounded device wait expired (error word %u); results of that launch are invalid", word);
 }
 

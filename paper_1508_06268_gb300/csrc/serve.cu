@@ -5,6 +5,8 @@
 // retired between graph launches and their observables kept until polled.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
 #include <condition_variable>
 #include <cstdlib>
 #include <cstring>
@@ -105,27 +107,48 @@ struct Slot {
 struct BatchShape {
   int G, GT;
 };
+using ShapeMap = std::map<int, BatchShape>;
 
-BatchShape batch_shape(int L) {
-  static std::map<int, BatchShape> shapes = [] {
-    std::map<int, BatchShape> m = {{64, {2, 2}}, {32, {8, 2}}, {16, {16, 1}}, {8, {16, 1}}};
-    // "L:G:GT,..." override (used by the launch-shape tuner)
-    if (const char *o = getenv("RFIM_BATCH_SHAPES")) {
-      std::string s(o);
-      size_t pos = 0;
-      while (pos < s.size()) {
-        int l = 0, g = 0, gt = 0;
-        if (sscanf(s.c_str() + pos, "%d:%d:%d", &l, &g, &gt) == 3 && batch_supported(l, gt) && g >= gt && g % gt == 0)
-          m[l] = {g, gt};
-        const size_t c = s.find(',', pos);
-        if (c == std::string::npos) break;
-        pos = c + 1;
-      }
-    }
-    return m;
-  }();
-  return shapes.at(L);
+// Built-in shapes, used until rfim_server_tune has measured better ones in this process.
+ShapeMap default_shapes() { return {{64, {2, 2}}, {32, {8, 2}}, {16, {16, 1}}, {8, {16, 1}}}; }
+
+bool shape_ok(int L, int G, int GT) {
+  return batch_supported(L, GT) && G >= GT && G % GT == 0 && G <= 1024 && batch_smem(L, G) <= (size_t)227 * 1024;
 }
+
+// "L:G:GT,..." over the defaults; false if an entry is malformed or names no batched instance.
+bool parse_shapes(const char *text, ShapeMap *out) {
+  ShapeMap m = default_shapes();
+  if (text && *text) {
+    const std::string str(text);
+    size_t pos = 0;
+    for (;;) {
+      int l = 0, g = 0, gt = 0, used = 0;
+      if (sscanf(str.c_str() + pos, "%d:%d:%d%n", &l, &g, &gt, &used) != 3 || !shape_ok(l, g, gt)) return false;
+      m[l] = {g, gt};
+      pos += (size_t)used;
+      if (pos >= str.size()) break;
+      if (str[pos] != ',') return false;
+      ++pos;
+    }
+  }
+  *out = m;
+  return true;
+}
+
+std::string format_shapes(const ShapeMap &m) {
+  std::string r;
+  for (auto it = m.rbegin(); it != m.rend(); ++it) {
+    if (!r.empty()) r += ",";
+    r += std::to_string(it->first) + ":" + std::to_string(it->second.G) + ":" + std::to_string(it->second.GT);
+  }
+  return r;
+}
+
+// Result of the last rfim_server_tune in this process (empty: none).
+std::mutex g_tuned_mu;
+std::string g_tuned_shapes;
+int g_tuned_intervals = 0;
 
 }  // namespace
 
@@ -139,6 +162,7 @@ struct rfim_server {
   SlotCtl *d_ctls = nullptr;
   BatchItem *d_items = nullptr;
   BatchQueue *d_queue = nullptr;
+  unsigned int *d_err = nullptr;  // device error word of the batched launches (debug-build checks)
   std::vector<Slot> slots;
   std::vector<SlotCtl> h_ctls;
   std::deque<Request> pending;
@@ -156,6 +180,7 @@ struct rfim_server {
   double busy_s = 0.0, attempts = 0.0;
   bool items_dirty = true;
   bool measure_xi = false;
+  ShapeMap shapes;  // (G, GT) per L of this server's batched launches
 };
 
 namespace {
@@ -231,6 +256,7 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
   xa.partFi = (long long *)take(R * 8);
   xa.partF = (double *)take(R * 8);
   xa.counter = (unsigned int *)take(4);
+  xa.err = s->d_err;
   double *kwave = nullptr;
   if (s->measure_xi) {
     xa.Fr = (double *)take(R * 8);
@@ -288,7 +314,7 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
                         ck(cudaMemcpyAsync((void *)xa.ksin, wave.data() + L, L * 8, cudaMemcpyHostToDevice, st), "tables"))) &&
             ck(cudaStreamSynchronize(st), "slot init");
   if (!ok) return RFIM_ECUDA;
-  const BatchShape sh = batch_shape(L);
+  const BatchShape sh = s->shapes.at(L);
   xa.J = (double)c.J;
   xa.h = (double)c.h;
   sl.desc = SlotDesc{};
@@ -441,6 +467,16 @@ void worker_loop(rfim_server *s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess)
       e = copy_sync(s, s->h_ctls.data(), s->d_ctls, sizeof(SlotCtl) * s->max_slots, cudaMemcpyDeviceToHost);
+    if (kDebugBuild && e == cudaSuccess) {  // debug build: bounds checks of this replay
+      unsigned int word = 0;
+      e = copy_sync(s, &word, s->d_err, 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && word) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->fatal = RFIM_EBOUNDS;
+        s->err = "batched launch: a bounds check of the debug build failed";
+        return;
+      }
+    }
     s->busy_s += seconds(t0, Clock::now());
     s->graph_launches += 1;
     if (e != cudaSuccess) {
@@ -464,7 +500,7 @@ void destroy_server(rfim_server *s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   if (s->graph) cudaGraphDestroy(s->graph);
-  void *ptrs[] = {s->arena.base, s->d_slots, s->d_ctls, s->d_items, s->d_queue};
+  void *ptrs[] = {s->arena.base, s->d_slots, s->d_ctls, s->d_items, s->d_queue, s->d_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -478,12 +514,23 @@ extern "C" {
 int rfim_server_create(const rfim_server_config *cfg, rfim_server **out) {
   if (!cfg || !out) return server_fail(nullptr, RFIM_EINVAL, "null argument");
   *out = nullptr;
-  if (cfg->max_slots < 1 || cfg->intervals_per_launch < 1 || cfg->mem_budget_bytes < (1u << 20))
+  if (cfg->max_slots < 1 || cfg->intervals_per_launch < 0 || cfg->mem_budget_bytes < (1u << 20))
     return server_fail(nullptr, RFIM_EINVAL, "invalid server configuration");
+  std::string tuned_shapes;
+  int tuned_k = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    tuned_shapes = g_tuned_shapes;
+    tuned_k = g_tuned_intervals;
+  }
+  ShapeMap shapes;
+  if (!parse_shapes(cfg->batch_shapes ? cfg->batch_shapes : tuned_shapes.c_str(), &shapes))
+    return server_fail(nullptr, RFIM_EINVAL, "batch_shapes: expected \"L:G:GT,...\" naming batched instances");
   rfim_server *s = new rfim_server();
   cudaGetDevice(&s->device);
+  s->shapes = shapes;
   s->max_slots = cfg->max_slots;
-  s->K = cfg->intervals_per_launch;
+  s->K = cfg->intervals_per_launch > 0 ? cfg->intervals_per_launch : (tuned_k > 0 ? tuned_k : 4);
   s->measure_xi = cfg->measure_xi != 0;
   s->slots.resize(s->max_slots);
   s->h_ctls.assign(s->max_slots, SlotCtl{});
@@ -503,12 +550,14 @@ int rfim_server_create(const rfim_server_config *cfg, rfim_server **out) {
   if ((e = cudaMalloc(&s->d_slots, sizeof(SlotDesc) * s->max_slots)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_ctls, sizeof(SlotCtl) * s->max_slots)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_items, sizeof(BatchItem) * nitems_max)) != cudaSuccess ||
-      (e = cudaMalloc(&s->d_queue, sizeof(BatchQueue))) != cudaSuccess)
+      (e = cudaMalloc(&s->d_queue, sizeof(BatchQueue))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_err, sizeof(unsigned int))) != cudaSuccess)
     return bail(RFIM_ENOMEM, std::string("tables: ") + cudaGetErrorString(e));
+  cudaMemsetAsync(s->d_err, 0, sizeof(unsigned int), s->stream);
   cudaMemsetAsync(s->d_ctls, 0, sizeof(SlotCtl) * s->max_slots, s->stream);
   cudaMemsetAsync(s->d_queue, 0, sizeof(BatchQueue), s->stream);
   cudaStreamSynchronize(s->stream);
-  for (int L : {8, 16, 32, 64}) s->smem = std::max(s->smem, batch_smem(L, batch_shape(L).G));
+  for (const auto &kv : s->shapes) s->smem = std::max(s->smem, batch_smem(kv.first, kv.second.G));
   if ((e = batch_prepare(s->smem)) != cudaSuccess) return bail(RFIM_ECUDA, std::string("attr: ") + cudaGetErrorString(e));
   int per_sm = 0, sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -608,6 +657,9 @@ int rfim_server_stats(rfim_server *s, rfim_server_info *out) {
   out->busy_s = s->busy_s;
   out->attempts = s->attempts;
   out->grid = s->grid;
+  out->intervals_per_launch = s->K;
+  const std::string sh = format_shapes(s->shapes);
+  snprintf(out->batch_shapes, sizeof out->batch_shapes, "%s", sh.c_str());
   return RFIM_OK;
 }
 
@@ -620,3 +672,150 @@ int rfim_server_destroy(rfim_server *s) {
 const char *rfim_server_last_error(const rfim_server *s) { return s ? s->err.c_str() : g_server_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Tuner of the batched kernel: launch shape (replicas per work item G, per thread GT) for each L,
+// then exchange intervals per graph replay, each timed closed-loop on scratch realizations.
+namespace {
+
+struct MixEntry {
+  int L, R;
+};
+
+// Wall-clock attempts/ns of `stream` submitted at once to a fresh server (second of two passes).
+int time_stream(const ShapeMap &shapes, int K, const std::vector<MixEntry> &stream, int32_t kind, int64_t sweeps,
+                int32_t ex, uint64_t budget, double *rate) {
+  const std::string sh = format_shapes(shapes);
+  rfim_server_config sc{};
+  sc.mem_budget_bytes = budget;
+  sc.max_slots = (int32_t)stream.size();
+  sc.intervals_per_launch = K;
+  sc.batch_shapes = sh.c_str();
+  rfim_server *s = nullptr;
+  int rc = rfim_server_create(&sc, &s);
+  if (rc != RFIM_OK) return rc;
+  *rate = 0.0;
+  for (int pass = 0; pass < 2 && rc == RFIM_OK; ++pass) {
+    std::vector<uint64_t> tickets;
+    double attempts = 0.0;
+    const Clock::time_point t0 = Clock::now();
+    for (size_t i = 0; i < stream.size() && rc == RFIM_OK; ++i) {
+      const int L = stream[i].L, R = stream[i].R;
+      std::vector<double> T(R);
+      for (int k = 0; k < R; ++k) T[k] = std::pow(5.0, (double)k / (double)(R - 1));  // geometric in [1, 5]
+      rfim_config c{};
+      c.L = L;
+      c.R = R;
+      c.R_capacity = R;
+      c.J = 1.0f;
+      c.h = 1.0f;
+      c.field_kind = kind;
+      c.field_seed = 1u + (uint32_t)i;
+      c.seed = 42u;
+      c.realization = (uint32_t)i;
+      c.temps = T.data();
+      c.layout = RFIM_LAYOUT_BITPACK;
+      uint64_t tk = 0;
+      rc = rfim_server_submit(s, &c, sweeps, ex, sweeps / ex / 2, &tk);
+      tickets.push_back(tk);
+      attempts += (double)L * L * L * R * (double)sweeps;
+    }
+    for (size_t i = 0; i < tickets.size() && rc == RFIM_OK; ++i) {
+      while ((rc = rfim_server_poll(s, tickets[i], nullptr, nullptr)) == RFIM_EBUSY)
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    const double dt = seconds(t0, Clock::now());
+    if (rc == RFIM_OK && pass == 1) *rate = attempts / (dt * 1e9);
+  }
+  if (rc != RFIM_OK) g_server_error = std::string("tuning stream: ") + rfim_server_last_error(s);
+  rfim_server_destroy(s);
+  return rc;
+}
+
+// The entries repeated until their work items (at replicas per item g_min) fill `items` CTAs.
+std::vector<MixEntry> fill_stream(const std::vector<MixEntry> &base, int g_min, int items) {
+  std::vector<MixEntry> out;
+  int have = 0;
+  while (have < items || out.size() < base.size()) {
+    const MixEntry &e = base[out.size() % base.size()];
+    out.push_back(e);
+    have += (e.R + g_min - 1) / g_min;
+  }
+  return out;
+}
+
+std::vector<BatchShape> shape_candidates(int L) {
+  switch (L) {
+    case 64: return {{2, 2}, {4, 2}, {2, 1}, {4, 1}, {1, 1}};
+    case 32: return {{8, 2}, {4, 2}, {16, 2}, {4, 1}, {8, 1}};
+    case 16: return {{16, 1}, {8, 1}, {32, 1}, {4, 1}};
+    default: return {{16, 1}, {32, 1}, {64, 1}, {8, 1}};
+  }
+}
+
+}  // namespace
+
+extern "C" int rfim_server_tune(const rfim_server_tune_config *t, char *shapes_out, int32_t cap, int32_t *intervals_out,
+                                double *attempts_per_ns) {
+  if (!t || t->n < 1 || !t->L || !t->R || t->exchange_every < 1 || t->sweeps < t->exchange_every ||
+      t->sweeps % t->exchange_every || t->mem_budget_bytes < (1u << 20) ||
+      !(t->field_kind == RFIM_FIELD_BIMODAL || t->field_kind == RFIM_FIELD_GAUSSIAN))
+    return server_fail(nullptr, RFIM_EINVAL, "rfim_server_tune: invalid configuration");
+  std::vector<MixEntry> mix;
+  for (int32_t i = 0; i < t->n; ++i) {
+    if (!bits_supported(t->L[i]) || t->R[i] < 2 || t->R[i] > kMaxServedR)
+      return server_fail(nullptr, RFIM_EINVAL, "rfim_server_tune: L must be 8, 16, 32 or 64 and R in [2, 1024]");
+    mix.push_back({t->L[i], t->R[i]});
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+  ShapeMap best = default_shapes();
+  for (int L : {64, 32, 16, 8}) {
+    std::vector<MixEntry> of_L;
+    for (const MixEntry &e : mix)
+      if (e.L == L) of_L.push_back(e);
+    if (of_L.empty()) continue;
+    int g_max = 1;
+    for (const BatchShape &c : shape_candidates(L)) g_max = std::max(g_max, c.G);
+    const std::vector<MixEntry> stream = fill_stream(of_L, g_max, 2 * sms);
+    double best_rate = -1.0;
+    for (const BatchShape &c : shape_candidates(L)) {
+      if (!shape_ok(L, c.G, c.GT)) continue;
+      ShapeMap m = best;
+      m[L] = c;
+      double r = 0.0;
+      const int rc = time_stream(m, 4, stream, t->field_kind, t->sweeps, t->exchange_every, t->mem_budget_bytes, &r);
+      if (rc != RFIM_OK) return rc;
+      if (r > best_rate) {
+        best_rate = r;
+        best[L] = c;
+      }
+    }
+  }
+  int g_max = 1;
+  for (const auto &kv : best) g_max = std::max(g_max, kv.second.G);
+  const std::vector<MixEntry> stream = fill_stream(mix, g_max, 2 * sms);
+  int best_k = 4;
+  double best_rate = -1.0;
+  for (int K : {1, 2, 4, 8}) {
+    double r = 0.0;
+    const int rc = time_stream(best, K, stream, t->field_kind, t->sweeps, t->exchange_every, t->mem_budget_bytes, &r);
+    if (rc != RFIM_OK) return rc;
+    if (r > best_rate) {
+      best_rate = r;
+      best_k = K;
+    }
+  }
+  const std::string text = format_shapes(best);
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned_shapes = text;
+    g_tuned_intervals = best_k;
+  }
+  if (shapes_out && cap > 0) snprintf(shapes_out, (size_t)cap, "%s", text.c_str());
+  if (intervals_out) *intervals_out = best_k;
+  if (attempts_per_ns) *attempts_per_ns = best_rate;
+  return RFIM_OK;
+}

@@ -158,3 +158,47 @@ def test_served_full_size_equals_oracle():
     np.testing.assert_array_equal(res["sums"], o.observables())
     np.testing.assert_array_equal(res["acc"], o.exchange_stats()[1])
     np.testing.assert_allclose(res["F"], o.observables_F(), rtol=1e-11, atol=1e-20)
+
+
+DEFAULT_SHAPES = "64:2:2,32:8:2,16:16:1,8:16:1"
+
+
+def test_tuned_server_gives_the_results_of_untuned_ones():
+    """Batched-kernel tuner (replicas per work item and per thread for each L, intervals per graph
+    replay): a server with the tuned settings, one with the built-in shapes and one with other
+    shapes serve the mix with identical results; the bimodal ones equal the oracle."""
+    tuned = rf.server_tune([(m[0], m[1]) for m in MIX], field_kind=rf.FIELD_GAUSSIAN, sweeps=20, exchange_every=10,
+                           mem_budget_bytes=256 << 20)
+    assert tuned["intervals_per_launch"] in (1, 2, 4, 8) and tuned["attempts_per_ns"] > 0
+    assert [int(x.split(":")[0]) for x in tuned["batch_shapes"].split(",")] == [64, 32, 16, 8]
+    runs = []
+    for shapes, k in ((None, 0), (DEFAULT_SHAPES, 4), ("64:1:1,32:4:1,16:4:1,8:8:1", 3)):
+        with rf.Server(mem_budget_bytes=256 << 20, max_slots=16, intervals_per_launch=k, measure_xi=True,
+                       batch_shapes=shapes) as srv:
+            st = srv.stats()
+            if shapes is None:  # the defaults are the tuner's choice
+                assert st["batch_shapes"] == tuned["batch_shapes"]
+                assert st["intervals_per_launch"] == tuned["intervals_per_launch"]
+            else:
+                assert st["batch_shapes"] == shapes and st["intervals_per_launch"] == k
+            tickets = [submit(srv, *m) for m in MIX]
+            runs.append([srv.wait(t) for t in tickets])
+    for other in runs[1:]:
+        for m, a, b in zip(MIX, runs[0], other):
+            for key in ("sums", "att", "acc", "F"):
+                np.testing.assert_array_equal(a[key], b[key], err_msg=f"{m} {key}")
+    for m, res in zip(MIX, runs[0]):
+        L, R, kind, real = m
+        if kind != rf.FIELD_BIMODAL:
+            continue
+        o = oracle.Oracle(L, inputs.geometric_temps(1.0, 5.0, R), h=1.5, field_kind=oracle.FIELD_BIMODAL,
+                          field_seed=10 + real, seed=42, realization=real)
+        o.run(SWEEPS, EX, 1)
+        np.testing.assert_array_equal(res["sums"], o.observables(), err_msg=str(m))
+
+
+@pytest.mark.parametrize("shapes", ["64:3:2", "64:2:4", "12:4:1", "64:2", "64:2:2;32:8:2", "64:16:2"])
+def test_invalid_batch_shapes_rejected(shapes):
+    with pytest.raises(rf.RfimError) as e:
+        rf.Server(mem_budget_bytes=16 << 20, max_slots=2, batch_shapes=shapes)
+    assert e.value.code == rf.EINVAL
