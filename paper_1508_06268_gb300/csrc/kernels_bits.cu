@@ -130,8 +130,8 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
 
 size_t grid_smem(int L, int G, int max_units) {
   const size_t PW = (size_t)L * L / 64;
-  const size_t need = (size_t)max_units * G * 2 * PW * 4 + (size_t)kGridMaxPieces * 2 * G * PW * 4 +
-                      tab_bytes(kGridMaxPieces * G);
+  // piece regions with two halo planes each (both colours), then the decision-table slots
+  const size_t need = (size_t)(max_units + 2 * kGridMaxPieces) * G * 2 * PW * 4 + tab_bytes(kGridMaxPieces * G);
   return std::max(need, kGridMinSmem);
 }
 

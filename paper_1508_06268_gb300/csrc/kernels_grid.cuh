@@ -54,6 +54,88 @@ __device__ __forceinline__ bool grid_wait(const unsigned *prog, int k, unsigned 
   return false;
 }
 
+// Hot loop of a round range of a half-sweep of the grid-wide kernel, kept out of line so that
+// its register allocation does not carry the kernel's set-up and schedule state.
+struct GridHot {
+  uint32_t *lat;
+  const float4 *field4;
+  uint32_t *bits;
+  const uint32_t *hbits;
+  uint32_t seed, realization, slot0;
+  int nb_items, np;
+  unsigned *err;
+  const uint32_t *desc;
+  const uint8_t *order;
+  const Piece *pc;
+  const int32_t *pcs, *pgact;
+};
+
+template <int L, bool BIM, int GG, int GTI>
+__device__ __noinline__ void grid_process(const GridHot hot, int i0, int i1, int c, uint32_t sweep, uint32_t tag) {
+  constexpr int PW = L * L / 64, W = L * L * L / 64;
+  constexpr int64_t WPAD = (W + 31) / 32 * 32;
+  constexpr int IPW = PW * (GG / GTI);
+  const int nt = blockDim.x, tid = threadIdx.x, other = c ^ 1;
+  const float4 *__restrict__ field4 = hot.field4;
+#pragma unroll 1
+  for (int it = i0 + tid; it < i1; it += nt) {
+    const uint32_t d = hot.desc[hot.order[it / IPW]];
+    const int w = it % PW;
+    const bool end_plane = it < hot.nb_items;
+    const int gb = (it % IPW) / PW * GTI;  // first replica of this item within the group
+    const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
+    if (!RFIM_DCHECK(hot.err, p < hot.np && zl < hot.pc[p].n, kDbgPartition)) continue;
+    const int z = hot.pc[p].z0 + zl;
+    const int64_t wq = (int64_t)z * PW + w;
+    const int gact = hot.pgact[p], cs = hot.pcs[p];
+    if (gb >= gact) continue;  // GTI = 1: replica past the end of a partial group
+    uint32_t *Pl = hot.lat + (d & 0x3FFFFu) + (zl + 1) * PW;  // plane zl of replica 0, colour 0
+    float4 hh4[8] = {};
+    if (!BIM) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
+    }
+    const uint32_t p0 = parity0_mask<L>(c, z, w);
+    PairSlices ps[GTI];
+    uint32_t sf[GTI], flip[GTI], fk[GTI][4];
+    const uint32_t fb = BIM ? hot.hbits[(int64_t)c * W + wq] : 0u;
+#pragma unroll
+    for (int gg = 0; gg < GTI; ++gg) {
+      const int g = min(gb + gg, gact - 1);
+      const uint32_t *O = Pl + (g * 2 + other) * cs;
+      uint32_t nbw[6], c0, c1, c2;
+      nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], p0, nbw[0], nbw[1], nbw[2], nbw[3]);
+      nbw[4] = O[PW + w];
+      nbw[5] = O[w - PW];
+      count6(nbw[0], nbw[1], nbw[2], nbw[3], nbw[4], nbw[5], c0, c1, c2);
+      sf[gg] = Pl[(g * 2 + c) * cs + w];
+      ps[gg] = make_pairs(c0, c1, c2, sf[gg], fb);
+      flip[gg] = 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fk[gg][q] = 0u;
+    }
+    const int r0 = hot.pc[p].g * GG;
+#pragma unroll kBlockUnroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = 7 - jj;
+#pragma unroll
+      for (int gg = 0; gg < GTI; ++gg) {
+        const int g = min(gb + gg, gact - 1);
+        const Words4 wd = philox10(hot.seed, hot.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), sweep, tag);
+        decide_block<BIM>(wd, ps[gg], j, hot.slot0 + (uint32_t)(p * GG + g) * kTabSlot, hh4[j], flip[gg], fk[gg]);
+      }
+    }
+#pragma unroll
+    for (int gg = 0; gg < GTI; ++gg) {
+      if (gb + gg >= gact) continue;
+      if (!BIM) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
+      const uint32_t nw = sf[gg] ^ flip[gg];
+      Pl[((gb + gg) * 2 + c) * cs + w] = nw;
+      if (end_plane) hot.bits[((int64_t)(r0 + gb + gg) * 2 + c) * W + wq] = nw;  // publish
+    }
+  }
+}
+
 template <int L, bool BIM, int GG, int GTI, int NT>
 __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
                                                         const float4 *__restrict__ field4, ExchArgs xa) {
@@ -61,17 +143,26 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
   extern __shared__ __align__(16) uint32_t sm[];
   const int k = blockIdx.x, nt = blockDim.x, tid = threadIdx.x;
+  // Shared-memory lattice: per piece p a region [GG replicas][2 colours][n_p + 2 planes][PW words]
+  // whose planes 0 and n_p + 1 are the z halos (the neighbouring CTAs' end planes), so that the
+  // z neighbours of every local plane are the planes before and after it.
   __shared__ Piece pc[kGridMaxPieces];
+  __shared__ int32_t pbase[kGridMaxPieces], pcs[kGridMaxPieces], pgact[kGridMaxPieces];
   __shared__ int np_s, nu_s, nb_s;
-  __shared__ int8_t plane_piece[256];
-  __shared__ uint8_t order[256];  // local planes: piece end planes first, then interior
+  __shared__ uint32_t udesc[256];  // per local unit: region base (words) | plane in piece << 18 | piece << 26
+  __shared__ uint8_t order[256];   // local units: piece end planes first, then interior
   if (tid == 0) {
     Piece tmp[kGridMaxPieces];
     const int np = grid_pieces(ga.gp, k, tmp);
-    int nu = 0;
+    int nu = 0, base = 0;
     for (int p = 0; p < np; ++p) {
       pc[p] = tmp[p];
-      for (int i = 0; i < tmp[p].n; ++i) plane_piece[tmp[p].lu0 + i] = (int8_t)p;
+      pbase[p] = base;
+      pcs[p] = (tmp[p].n + 2) * PW;
+      pgact[p] = min(GG, v.R - tmp[p].g * GG);
+      for (int i = 0; i < tmp[p].n && tmp[p].lu0 + i < 256; ++i)
+        udesc[tmp[p].lu0 + i] = (uint32_t)base | ((uint32_t)i << 18) | ((uint32_t)p << 26);
+      base += GG * 2 * (tmp[p].n + 2) * PW;
       nu += tmp[p].n;
     }
     int o = 0;
@@ -92,19 +183,18 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
                                                nb_s <= nu_s,
                                    kDbgPartition);
   const int np = part_ok ? np_s : 0, nu = part_ok ? nu_s : 0, nb = part_ok ? nb_s : 0;
-  uint32_t *lat = sm;                                          // [max_units][GG][2][PW]
-  uint32_t *halo = lat + (size_t)ga.max_units * GG * 2 * PW;  // [pieces][2][GG][PW] (other colour)
-  uint32_t *tab = halo + (size_t)kGridMaxPieces * 2 * GG * PW;  // [pieces][GG] decision-table slots
+  uint32_t *lat = sm;                                                   // piece regions
+  uint32_t *tab = lat + (size_t)(ga.max_units + 2 * kGridMaxPieces) * GG * 2 * PW;  // [pieces][GG] table slots
   const uint32_t slot0 = tab_slot0(tab);
-  auto lat_at = [&](int lu, int gg, int c) { return lat + ((size_t)(lu * GG + gg) * 2 + c) * PW; };
-  auto halo_at = [&](int p, int side, int gg) { return halo + ((size_t)(p * 2 + side) * GG + gg) * PW; };
-  auto gact_of = [&](int p) { return min(GG, v.R - pc[p].g * GG); };
+  // word w of plane zl (-1 .. n_p: halos included) of colour c of replica gg in piece p
+  auto at = [&](int p, int gg, int c, int zl) { return lat + pbase[p] + (gg * 2 + c) * pcs[p] + (zl + 1) * PW; };
 
   for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
     const int lu = t / (GG * 2 * PW), rem = t % (GG * 2 * PW), gg = rem / (2 * PW), c = (rem / PW) & 1, w = rem % PW;
-    const Piece &q = pc[plane_piece[lu]];
-    const int r = q.g * GG + gg, z = q.z0 + (lu - q.lu0);
-    lat[t] = r < v.R ? v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] : 0u;
+    const uint32_t d = udesc[lu];
+    const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
+    const int r = pc[p].g * GG + gg, z = pc[p].z0 + zl;
+    at(p, gg, c, zl)[w] = r < v.R ? v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] : 0u;
   }
   tab_fill<BIM>(v, tab, slot0, np * GG, [&](int t) { return min(pc[t / GG].g * GG + t % GG, v.R - 1); });
   __syncthreads();
@@ -118,10 +208,10 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   const int idle_warps = items > split ? nt / 32 - busy_warps : 0;
   unsigned *err = xa.err;
 
-  // Loads the `other` colour's end planes of every piece's z neighbours once their CTAs have
-  // published `need` half-sweeps: thread `lead` waits, the group of `count` threads (whole warps,
-  // named barrier `bar`) holding it then loads.  The caller makes the loads visible with a CTA
-  // barrier.
+  // Loads the colour-`other` end planes of every piece's z neighbours into its halo planes once
+  // their CTAs have published `need` half-sweeps: thread `lead` waits, the group of `count`
+  // threads (whole warps, named barrier `bar`) holding it then loads.  The caller makes the loads
+  // visible with a CTA barrier.
   auto fetch_halos = [&](int other, unsigned need, int t0, int count, int bar) {
     const int lt = tid - t0;
     if (lt == 0) {
@@ -139,80 +229,35 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
       const int p = t / (2 * GG * PW), side = (t / (GG * PW)) & 1, gg = (t / PW) % GG, w = t % PW;
       const int r = min(pc[p].g * GG + gg, v.R - 1);
       const int z = side ? (pc[p].z0 + pc[p].n) % L : (pc[p].z0 + L - 1) % L;
-      halo[t] = __ldcg(v.bits + ((int64_t)r * 2 + other) * W + (int64_t)z * PW + w);
+      at(p, gg, other, side ? pc[p].n : -1)[w] = __ldcg(v.bits + ((int64_t)r * 2 + other) * W + (int64_t)z * PW + w);
     }
   };
   // the neighbours' colour-1 end planes as the launch found them
   fetch_halos(1, 0u, 0, nt, 1);
   __syncthreads();
-
-  // z-neighbour words (other colour) of local plane lu, word w, replica gg
-  auto zn = [&](int lu, int w, int gg, int other, uint32_t &up, uint32_t &dn) {
-    const int p = plane_piece[lu];
-    const int pl = lu - pc[p].lu0;
-    up = pl + 1 < pc[p].n ? lat_at(lu + 1, gg, other)[w] : halo_at(p, 1, gg)[w];
-    dn = pl > 0 ? lat_at(lu - 1, gg, other)[w] : halo_at(p, 0, gg)[w];
-  };
+  GridHot hot;
+  hot.lat = lat;
+  hot.field4 = field4;
+  hot.bits = v.bits;
+  hot.hbits = v.hbits;
+  hot.seed = v.seed;
+  hot.realization = v.realization;
+  hot.slot0 = slot0;
+  hot.nb_items = nb * IPW;
+  hot.np = np;
+  hot.err = err;
+  hot.desc = udesc;
+  hot.order = order;
+  hot.pc = pc;
+  hot.pcs = pcs;
+  hot.pgact = pgact;
 
   for (int h = 0; h < 2 * nsw; ++h) {
     const int c = h & 1, other = c ^ 1;
     const uint32_t sweep = sweep0 + (uint32_t)(h >> 1);
     const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)c);
     auto process = [&](int i0, int i1) {
-#pragma unroll 1
-      for (int it = i0 + tid; it < i1; it += nt) {
-        const int lu = order[it / IPW], w = it % PW;
-        const bool end_plane = it < nb * IPW;
-        const int gb = (it % IPW) / PW * GTI;  // first replica of this item within the group
-        const int p = plane_piece[lu];
-        if (!RFIM_DCHECK(err, lu < nu && p >= 0 && p < np && pc[p].z0 + (lu - pc[p].lu0) < L, kDbgPartition)) continue;
-        const int z = pc[p].z0 + (lu - pc[p].lu0);
-        const int64_t wq = (int64_t)z * PW + w;
-        const int gact = gact_of(p);
-        if (gb >= gact) continue;  // GTI = 1: replica past the end of a partial group
-        float4 hh4[8] = {};
-        if (!BIM) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) hh4[j] = __ldg(field4 + field4_index(c, wq, j, WPAD));
-        }
-        const uint32_t p0 = parity0_mask<L>(c, z, w);
-        PairSlices ps[GTI];
-        uint32_t sf[GTI], flip[GTI], fk[GTI][4];
-        const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
-#pragma unroll
-        for (int gg = 0; gg < GTI; ++gg) {
-          const int g = min(gb + gg, gact - 1);
-          const uint32_t *O = lat_at(lu, g, other);
-          uint32_t nbw[6], c0, c1, c2;
-          nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], p0, nbw[0], nbw[1], nbw[2], nbw[3]);
-          zn(lu, w, g, other, nbw[4], nbw[5]);
-          count6(nbw[0], nbw[1], nbw[2], nbw[3], nbw[4], nbw[5], c0, c1, c2);
-          sf[gg] = lat_at(lu, g, c)[w];
-          ps[gg] = make_pairs(c0, c1, c2, sf[gg], fb);
-          flip[gg] = 0u;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) fk[gg][q] = 0u;
-        }
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = 7 - jj;
-#pragma unroll
-          for (int gg = 0; gg < GTI; ++gg) {
-            const int g = min(gb + gg, gact - 1);
-            const int r = pc[p].g * GG + g;
-            const Words4 wd = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)r, sweep, tag);
-            decide_block<BIM>(wd, ps[gg], j, slot0 + (uint32_t)(p * GG + g) * kTabSlot, hh4[j], flip[gg], fk[gg]);
-          }
-        }
-#pragma unroll
-        for (int gg = 0; gg < GTI; ++gg) {
-          if (gb + gg >= gact) continue;
-          if (!BIM) flip[gg] = fk[gg][0] | (fk[gg][1] << 8) | (fk[gg][2] << 16) | (fk[gg][3] << 24);
-          const uint32_t nw = sf[gg] ^ flip[gg];
-          lat_at(lu, gb + gg, c)[w] = nw;
-          if (end_plane) v.bits[((int64_t)(pc[p].g * GG + gb + gg) * 2 + c) * W + wq] = nw;  // publish
-        }
-      }
+      grid_process<L, BIM, GG, GTI>(hot, i0, i1, c, sweep, tag);
     };
     // end planes (and the interior items sharing their rounds), then the progress word: the CTA
     // barrier orders every thread's end-plane stores before thread 0's gpu-scope fence and release
@@ -237,34 +282,36 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
 
   for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
     const int lu = t / (GG * 2 * PW), rem = t % (GG * 2 * PW), gg = rem / (2 * PW), c = (rem / PW) & 1, w = rem % PW;
-    const Piece &q = pc[plane_piece[lu]];
-    const int r = q.g * GG + gg, z = q.z0 + (lu - q.lu0);
-    if (r < v.R) v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = lat[t];
+    const uint32_t d = udesc[lu];
+    const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
+    const int r = pc[p].g * GG + gg, z = pc[p].z0 + zl;
+    if (r < v.R) v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = at(p, gg, c, zl)[w];
   }
   if (!xa.enabled) return;
 
   // ---- energy partials (Eq. 1) per (replica, piece), then the exchange tail ----------------
-  // (the halo buffer holds the neighbours' final colour-1 end planes, fetched by the last half-sweep)
+  // (the colour-1 halo planes hold the neighbours' final end planes, fetched by the last half-sweep)
   __shared__ long long red_i[3][32];
   __shared__ double red_d[32];
   __shared__ int last_cta;
   const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
   for (int p = 0; p < np; ++p) {
-    const int gact = gact_of(p);
+    const int gact = pgact[p];
     for (int gg = 0; gg < gact; ++gg) {
       long long b = 0, m = 0, fi = 0;
       float fs = 0.f, fe = 0.f;
       for (int t = tid; t < pc[p].n * 2 * PW; t += nt) {
         const int c = t / (pc[p].n * PW), rem = t % (pc[p].n * PW), pl = rem / PW, w = rem % PW;
-        const int lu = pc[p].lu0 + pl, z = pc[p].z0 + pl;
+        const int z = pc[p].z0 + pl;
         const int64_t wq = (int64_t)z * PW + w;
-        const uint32_t self = lat_at(lu, gg, c)[w];
+        const uint32_t self = at(p, gg, c, pl)[w];
         m += 2 * __popc(self) - 32;
         if (c == 0) {
-          const uint32_t *O = lat_at(lu, gg, 1);
+          const uint32_t *O = at(p, gg, 1, pl);
           uint32_t nbw[6];
           nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], parity0_mask<L>(0, z, w), nbw[0], nbw[1], nbw[2], nbw[3]);
-          zn(lu, w, gg, 1, nbw[4], nbw[5]);
+          nbw[4] = O[PW + w];
+          nbw[5] = O[w - PW];
 #pragma unroll
           for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nbw[d]);
         }
