@@ -40,9 +40,9 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 MULWIDE_PER_CLK_SM = 32.0
 MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
-# (bit layout: one exchange interval, 3.36e8 attempts; int8: one half-sweep, 1.68e7 attempts) from
+# (one exchange interval, 3.36e8 attempts, in either layout) from
 # one ncu capture of the current kernel version; None when the kernel changed since the capture.
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_halfsweep_int8_rows8": None}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_sweeps_bits (int8 layout staged as bits)": None}
 
 
 def parse():
@@ -531,7 +531,8 @@ def roofline_of(m, layout, rf, props, steps):
     achieved = L ** 3 * R * EX / (group_ms * 1e6)  # Gattempts/s
     sm_mhz = clk["sm_mhz"] or 2070.0
     peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
-    kernel = "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_halfsweep_int8_rows8"
+    # the int8 layout at L = 64 runs the same kernel with its slabs staged from bytes into bits
+    kernel = "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_sweeps_bits (int8 layout staged as bits)"
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s", "frac": achieved / peak,
             "traffic": SWEEP_TRAFFIC_BYTES.get(kernel), "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
             "kernel": kernel,

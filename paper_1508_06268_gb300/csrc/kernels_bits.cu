@@ -26,8 +26,10 @@ KernelFn pick(bool bim) {
   return bim ? (KernelFn)k_sweeps_bits<L, S, GT, true, NT> : (KernelFn)k_sweeps_bits<L, S, GT, false, NT>;
 }
 
-// Instances available to launch plans (L, cluster size S, replicas per thread GT, threads NT).
-KernelFn kernel_for(int L, int S, int GT, int NT, bool bim) {
+// Instances available to launch plans (L, cluster size S, replicas per thread GT, threads NT);
+// i8: the int8-layout staging instances (kernels_bits_i8.cu), default shapes only.
+KernelFn kernel_for(int L, int S, int GT, int NT, bool bim, bool i8 = false) {
+  if (i8) return (KernelFn)kernel_for_i8(L, S, GT, NT, bim);
 #define RFIM_BITS_INSTANCE(l, s_, gt, nt) \
   if (L == l && S == s_ && GT == gt && NT == nt) return pick<l, s_, gt, nt>(bim);
   RFIM_BITS_INSTANCE(64, 1, 1, 512)
@@ -197,13 +199,16 @@ std::vector<std::string> plan_candidates(int32_t L) {
   return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
 }
 
-int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err) {
+int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err, bool i8) {
   BitsPlan p;
   p.L = L;
   p.Rcap = Rcap;
+  p.i8 = i8;
   int sms_dev = 0;
   cudaDeviceGetAttribute(&sms_dev, cudaDevAttrMultiProcessorCount, 0);
-  if (L == 64) {
+  if (L == 64 && i8) {
+    p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;  // int8 staging: the cluster shape only
+  } else if (L == 64) {
     // clusters of 4 z slabs x 4 replicas, unless they would leave more than a fifth of the SMs
     // idle (e.g. R = 70 after adaptation: 72 CTAs) or need more clusters than fit at once (a
     // second wave; 36 clusters of 4 at one CTA per SM on GB300); then the grid-wide plan
@@ -254,8 +259,8 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
     // ignored and the defaults stand
     const bool named = sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4;
-    const bool exists = named && (s == 0 ? (th >= 256 && th <= 1024 && th % 32 == 0 && grid_kernel_for(L, g, gt, th, bimodal))
-                                         : kernel_for(L, s, gt, th, bimodal) != nullptr);
+    const bool exists = named && (s == 0 ? (!i8 && th >= 256 && th <= 1024 && th % 32 == 0 && grid_kernel_for(L, g, gt, th, bimodal))
+                                         : kernel_for(L, s, gt, th, bimodal, i8) != nullptr);
     if (exists) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th;
     }
@@ -267,7 +272,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal);
+  KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal, i8);
   GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.G, p.GT, p.threads, bimodal) : nullptr;
   if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
@@ -400,7 +405,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   }
   const bool multihit = mh && mh->mh > 0;
   if (multihit && plan.S == 0) return cudaErrorInvalidConfiguration;
-  KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal);
+  KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, plan.i8);
   MhFn mfn = multihit ? mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, mh->tile) : nullptr;
   if (!fn && !mfn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;

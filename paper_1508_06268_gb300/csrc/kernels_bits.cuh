@@ -532,6 +532,19 @@ __device__ __forceinline__ void update_word(const RealView &v, uint32_t *sp, int
   }
 }
 
+// int8 layout staged as bits: the 32 sites q = 32 wq + p (p = 4j + k) of a bit-layout word are
+// the 32 consecutive 0/1 bytes at spins8 + 32 wq of the same colour; byte 4j + k goes to bit 8k + j,
+// i.e. the word is the OR of the eight 4-byte groups shifted by j.
+__device__ __forceinline__ uint32_t pack_int8_word(const uint8_t *p32) {
+  const uint4 a = *reinterpret_cast<const uint4 *>(p32), b = *reinterpret_cast<const uint4 *>(p32 + 16);
+  return a.x | (a.y << 1) | (a.z << 2) | (a.w << 3) | (b.x << 4) | (b.y << 5) | (b.z << 6) | (b.w << 7);
+}
+__device__ __forceinline__ void unpack_int8_word(uint32_t w, uint8_t *p32) {
+  const uint32_t m = 0x01010101u;
+  *reinterpret_cast<uint4 *>(p32) = make_uint4(w & m, (w >> 1) & m, (w >> 2) & m, (w >> 3) & m);
+  *reinterpret_cast<uint4 *>(p32 + 16) = make_uint4((w >> 4) & m, (w >> 5) & m, (w >> 6) & m, (w >> 7) & m);
+}
+
 // Copies the slab (both colours) of replicas [r0, r0 + gact) between global and shared memory.
 template <int L, int S, bool TO_SHARED>
 __device__ __forceinline__ void copy_slab(const RealView &v, uint32_t *sp, int r0, int gact, int z0) {
@@ -550,7 +563,9 @@ __device__ __forceinline__ void copy_slab(const RealView &v, uint32_t *sp, int r
 // One exchange interval of replicas [r0, r0 + gact) of realization v, slab `rank` of S: load into
 // shared memory, nsw sweeps, write back, and (xa.enabled) the energy partials and the exchange
 // tail.  All threads of the CTA call it; blockDim.x threads, dynamic shared memory >= the plan's.
-template <int L, int S, int GT, bool BIM, bool XI = false>
+// I8: the realization is stored in the int8 layout (v.spins8) and staged here as bits: the slab is
+// packed into shared memory on entry and unpacked back on exit (a word is 32 consecutive bytes).
+template <int L, int S, int GT, bool BIM, bool XI = false, bool I8 = false>
 __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, int gact, int rank, uint32_t sweep0,
                                               int nsw, const float4 *__restrict__ field4, const ExchArgs &xa) {
   using Gm = BitsGeom<L>;
@@ -575,7 +590,8 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
                   RFIM_DCHECK(xa.err, S == 1 || (cluster_ctas() == (uint32_t)S && up_rank < S && dn_rank < S), kDbgRank);
   for (int t = tid; ok && t < gact * 2 * WC; t += nt) {
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
-    sp[t] = v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl];
+    const int64_t gw = ((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl;
+    sp[t] = I8 ? pack_int8_word(v.spins8 + 32 * gw) : v.bits[gw];
   }
   if (ok) tab_fill<BIM>(v, tab, slot0, gact, [&](int g) { return r0 + g; });
   sync_slabs<S>();
@@ -651,19 +667,23 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
 
   for (int t = tid; ok && t < gact * 2 * WC; t += nt) {
     const int g = t / (2 * WC), rem = t % (2 * WC), c = rem / WC, wl = rem % WC;
-    v.bits[((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl] = sp[t];
+    const int64_t gw = ((int64_t)(r0 + g) * 2 + c) * W + (int64_t)z0 * P + wl;
+    if (I8)
+      unpack_int8_word(sp[t], v.spins8 + 32 * gw);
+    else
+      v.bits[gw] = sp[t];
   }
   if (xa.enabled) interval_tail<L, S, BIM, XI>(v, G, r0, ok ? gact : 0, rank, nsw, field4, xa);
 }
 
-template <int L, int S, int GT, bool BIM, int NT>
+template <int L, int S, int GT, bool BIM, int NT, bool I8 = false>
 __global__ void __launch_bounds__(NT) k_sweeps_bits(RealView v, int32_t G, uint32_t sweep0, int32_t nsw,
                                                      const float4 *__restrict__ field4, ExchArgs xa) {
   const int rank = S > 1 ? (int)cluster_rank() : 0;
   const int r0 = (int)(blockIdx.x / S) * G;
   const int gact = min(G, v.R - r0);
   xa.expected = gridDim.x;
-  bits_interval<L, S, GT, BIM>(v, G, r0, gact, rank, sweep0, nsw, field4, xa);
+  bits_interval<L, S, GT, BIM, false, I8>(v, G, r0, gact, rank, sweep0, nsw, field4, xa);
 }
 
 }  // namespace rfim

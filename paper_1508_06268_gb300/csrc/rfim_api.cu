@@ -199,7 +199,7 @@ int reset_state(rfim_ctx *c, uint32_t stage) {
 // checks of the debug build as RFIM_EBOUNDS; the word is cleared once reported.  Synchronises the
 // stream.
 int check_device_error(rfim_ctx *c) {
-  if (c->layout != RFIM_LAYOUT_BITPACK || !c->plan.counter) return RFIM_OK;
+  if (!c->plan.counter) return RFIM_OK;  // no bit-layout plan (int8 kernels of other L)
   unsigned int word = 0;
   CUDA_OR_FAIL(c, cudaMemcpyAsync(&word, c->plan.counter + 1, 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
@@ -215,7 +215,7 @@ int do_sweeps(rfim_ctx *c, int64_t n) {
   RealView v = view_of(c);
   cudaEvent_t stop;
   CUDA_OR_FAIL(c, prof_begin(c, 0, &stop));
-  if (c->layout == RFIM_LAYOUT_BITPACK) {
+  if (c->plan.counter) {  // bit layout, or the int8 layout staged as bits
     CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, false, 0u, 0, (double)c->J,
                                        (double)c->h, c->stream, &c->mh));
     c->launches += 1;
@@ -256,7 +256,7 @@ int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from) {
 }
 
 int do_exchange(rfim_ctx *c, int64_t measure_from) {
-  if (c->layout == RFIM_LAYOUT_BITPACK) return do_sweeps_exchange_bits(c, 0, measure_from);
+  if (c->plan.counter) return do_sweeps_exchange_bits(c, 0, measure_from);
   RealView v = view_of(c);
   cudaEvent_t stop;
   CUDA_OR_FAIL(c, prof_begin(c, 1, &stop));
@@ -279,7 +279,7 @@ int do_run(rfim_ctx *c, int64_t n_sweeps, int32_t ex, int64_t measure_from) {
     }
     const bool ends_interval = ex > 0 && (c->sweep + chunk) % ex == 0;
     int rc;
-    if (ends_interval && c->layout == RFIM_LAYOUT_BITPACK) {
+    if (ends_interval && c->plan.counter) {
       rc = do_sweeps_exchange_bits(c, chunk, measure_from);
       if (rc) return rc;
       left -= chunk;
@@ -365,10 +365,14 @@ int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
     delete c;
     return code;
   };
+  // int8 layout with L in {8, 16, 32, 64}: stored as bytes, swept by the bit-layout kernels that
+  // stage each slab as bits in shared memory (kernels_bits_i8.cu)
+  const bool staged_i8 = cfg->layout == RFIM_LAYOUT_INT8 && bits_supported(L);
   if (c->layout == RFIM_LAYOUT_BITPACK) {
     if ((rc = dalloc(c, &c->bits, (size_t)Rcap * N / 32))) return bail(rc);
     if ((rc = dalloc(c, &c->hbits, N / 32))) return bail(rc);
   } else {
+    if (staged_i8 && (rc = dalloc(c, &c->hbits, N / 32))) return bail(rc);
     if ((rc = dalloc(c, &c->spins8, (size_t)Rcap * N))) return bail(rc);
     const size_t parts = (size_t)Rcap * kEnergyMaxParts;
     if ((rc = dalloc(c, &c->eparts.B, parts))) return bail(rc);
@@ -396,8 +400,8 @@ int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
   if ((rc = dalloc(c, &c->obs, (size_t)Rcap * 5))) return bail(rc);
   if ((rc = dalloc(c, &c->n_meas, 1))) return bail(rc);
   (void)half;
-  if (c->layout == RFIM_LAYOUT_BITPACK) {
-    if ((rc = make_bits_plan(L, Rcap, c->kind == kBimodal, &c->plan, &c->err))) return bail(rc);
+  if (c->layout == RFIM_LAYOUT_BITPACK || staged_i8) {
+    if ((rc = make_bits_plan(L, Rcap, c->kind == kBimodal, &c->plan, &c->err, staged_i8))) return bail(rc);
   }
   if (c->kind == RFIM_FIELD_EXPLICIT) {
     cudaError_t e = cudaMemcpyAsync(c->hraw, cfg->field, N * 4, cudaMemcpyHostToDevice, c->stream);
@@ -410,7 +414,7 @@ int rfim_create(const rfim_config *cfg, rfim_ctx **out) {
     cudaError_t e = launch_field(v, c->kind, c->field_seed, c->h, c->hraw, c->hh_c, c->hbit_c, c->hbits, c->stream);
     if (e != cudaSuccess) return bail(fail(c, RFIM_ECUDA, "field kernel: %s", cudaGetErrorString(e)));
     c->launches += c->hbits ? 2 : 1;
-    if (c->layout == RFIM_LAYOUT_BITPACK && c->plan.field4) {
+    if (c->plan.field4) {
       e = build_field4(v, c->plan, c->stream);
       if (e != cudaSuccess) return bail(fail(c, RFIM_ECUDA, "field4 kernel: %s", cudaGetErrorString(e)));
       c->launches += 1;
@@ -457,7 +461,7 @@ int rfim_adapt_temps(rfim_ctx *ctx, int32_t n_trials, int64_t sweeps_per_trial, 
   const int64_t R_final = (int64_t)c->R + (int64_t)n_trials * inserts_per_trial;
   if (R_final > c->Rcap) return fail(c, RFIM_EINVAL, "R_final %lld exceeds R_capacity %d", (long long)R_final, c->Rcap);
   if (temps_out && temps_cap < R_final) return fail(c, RFIM_EINVAL, "temps_cap %d < R_final %lld", temps_cap, (long long)R_final);
-  if (c->layout == RFIM_LAYOUT_BITPACK && !bits_plan_fits(c->plan, (int32_t)R_final))
+  if (c->plan.counter && !bits_plan_fits(c->plan, (int32_t)R_final))
     return fail(c, RFIM_EINVAL, "R_final %lld not supported by the bit-layout plan", (long long)R_final);
   int rc;
   for (int32_t t = 1; t <= n_trials; ++t) {
