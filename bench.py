@@ -8,9 +8,10 @@ runs on the GPU.  Steps continue the same Markov chain.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--layout bitpack|int8]
 
-The JSON line also carries the other spin layout of the same workload (int8 by default) and a
+The JSON line also carries the other spin layout of the same workload (int8 by default), a
 serving measurement (continuous batching vs per-realization launches on a C5-shaped stream of
-128 realizations x 1000 sweeps, batched kernel tuned first).
+128 realizations x 1000 sweeps, batched kernel tuned first) and the smaller configurations C1-C3
+(C3 with its temperature adaptation and 10^5 production sweeps).
 
 Under torchrun each rank runs its own realization (realization id = rank; weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -42,7 +43,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
 # (one exchange interval, 3.36e8 attempts, in either layout) from
 # one ncu capture of the current kernel version; None when the kernel changed since the capture.
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325824e6, "k_sweeps_bits (int8 layout staged as bits)": None}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 5.325568e6, "k_sweeps_bits (int8 layout staged as bits)": 34.692352e6}
 
 
 def parse():
@@ -59,6 +60,7 @@ def parse():
     p.add_argument("--profile-case", default="c4", choices=["c4", "c4-bimodal", "c4-int8", "serve", "multihit"])
     p.add_argument("--no-int8", action="store_true", help="skip the int8-layout sub-measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving sub-measurement")
+    p.add_argument("--no-configs", action="store_true", help="skip the C1-C3 sub-measurement")
     p.add_argument("--serve-realizations", type=int, default=128)
     p.add_argument("--adapt-L", type=int, default=32)
     p.add_argument("--realizations", type=int, default=128)
@@ -481,6 +483,56 @@ def run_int_rates():
         subprocess.run([exe], check=True)
 
 
+def configs_measure(rf, torch):
+    """The smaller benchmark configurations end to end on the device (bit layout, CUDA events on
+    the context's stream): C1 L=8 Gaussian R=16 [1.5,5] 2000 sweeps / ex 10; C2 L=16 bimodal
+    h=1.5 R=32 [1,5] 10^4 sweeps / ex 5; C3 L=32 Gaussian R0=64 [1,5] adapted by 3 trials of 2000
+    sweeps (ex 10, 2 insertions each: R=70), then 10^5 production sweeps / ex 10.  Each run is
+    preceded by a short warm-up run of the same shape."""
+    from paper_1508_06268_gb300 import inputs
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) * 1e-3
+
+    out = {}
+    for name, Lc, kind, h, T, sweeps, ex in (
+            ("C1", 8, rf.FIELD_GAUSSIAN, 1.0, inputs.geometric_temps(1.5, 5.0, 16), 2000, 10),
+            ("C2", 16, rf.FIELD_BIMODAL, 1.5, inputs.geometric_temps(1.0, 5.0, 32), 10_000, 5)):
+        g = rf.Realization(Lc, T, h=h, field_kind=kind, field_seed=1, seed=42, layout=rf.LAYOUT_BITPACK)
+        g.run(10 * ex, ex, 0)
+        g.close()
+        g = rf.Realization(Lc, T, h=h, field_kind=kind, field_seed=1, seed=42, layout=rf.LAYOUT_BITPACK)
+        _, dt = timed(lambda: g.run(sweeps, ex, sweeps // ex // 2))
+        g.observables()
+        g.close()
+        out[name] = {"attempts_per_ns": Lc ** 3 * len(T) * sweeps / (dt * 1e9), "seconds": dt,
+                     "L": Lc, "R": len(T), "sweeps": sweeps}
+    T0 = inputs.geometric_temps(1.0, 5.0, 64)
+    w = rf.Realization(32, T0, field_kind=rf.FIELD_GAUSSIAN, field_seed=1, seed=42, layout=rf.LAYOUT_BITPACK,
+                       R_capacity=70)
+    w.adapt_temps(1, 100, 10, 2)
+    w.run(1000, 10, 0)
+    w.close()
+    g = rf.Realization(32, T0, field_kind=rf.FIELD_GAUSSIAN, field_seed=1, seed=42, layout=rf.LAYOUT_BITPACK,
+                       R_capacity=70)
+    Ta, dt_a = timed(lambda: g.adapt_temps(3, 2000, 10, 2))
+    _, dt_p = timed(lambda: g.run(100_000, 10, 5000))
+    g.observables()
+    g.close()
+    trial_attempts = 32 ** 3 * (64 + 66 + 68) * 2000
+    out["C3"] = {"attempts_per_ns": 32 ** 3 * len(Ta) * 100_000 / (dt_p * 1e9), "seconds": dt_p,
+                 "adapt_seconds": dt_a, "adapt_attempts_per_ns": trial_attempts / (dt_a * 1e9),
+                 "L": 32, "R": len(Ta), "sweeps": 100_000}
+    return out
+
+
 def measure_layout(rf, torch, layout, args, T, real, field_seed, local, dist):
     """W untimed steps, then K timed steps (L2 flushed before each) of the C4 workload in one
     layout; returns the device time (max over ranks), wall time, kernel profile, launches, clocks."""
@@ -600,6 +652,9 @@ def main():
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
         serving = serve_measure(args.serve_realizations, 1000, tune=True, with_xi=False)
+    small = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        small = configs_measure(rf, torch)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -615,7 +670,7 @@ def main():
                        "parallelism": f"realization per GPU x{world}",
                        "wall_s": m["wall"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches"],
-            "clocks": m["clk"], "serving": serving,
+            "clocks": m["clk"], "serving": serving, "configs": small,
         }
         if other is not None:  # the second layout of the C4 workload under its own name
             line[other["layout"]] = other
