@@ -9,7 +9,6 @@
 #include <vector>
 
 #include "kernels_bits.cuh"
-#include "kernels_ws.cuh"
 #include "kernels_grid.cuh"
 #include "kernels_mh.cuh"
 #include "lattice.cuh"
@@ -52,11 +51,6 @@ KernelFn kernel_for(int L, int S, int GT, int NT, bool bim, bool i8 = false) {
   RFIM_BITS_INSTANCE(8, 1, 1, 128)
   RFIM_BITS_INSTANCE(8, 1, 1, 512)
 #undef RFIM_BITS_INSTANCE
-  // warp-specialised variant (GT = 4, kWsThreads threads): selected by threads == kWsThreads
-  if (NT == kWsThreads && GT == kWsGT) {
-    if (L == 64 && S == 4) return bim ? (KernelFn)k_sweeps_ws<64, 4, true> : (KernelFn)k_sweeps_ws<64, 4, false>;
-    if (L == 64 && S == 2) return bim ? (KernelFn)k_sweeps_ws<64, 2, true> : (KernelFn)k_sweeps_ws<64, 2, false>;
-  }
   return nullptr;
 }
 
@@ -193,7 +187,7 @@ void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &
 
 std::vector<std::string> plan_candidates(int32_t L) {
   if (L == 64)
-    return {"4,4,4,512", "0,4,4,512", "0,4,1,512", "4,4,4,768", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
+    return {"4,4,4,512", "0,4,4,512", "0,4,1,512", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
   if (L == 32) return {"2,1,1,256", "4,1,1,128", "1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512", "0,4,1,512"};
   if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
   return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
@@ -293,8 +287,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     p.smem = grid_smem(L, p.G, maxu);
   }
   if (!gfn)
-    p.smem = p.threads == kWsThreads ? ws_smem(L, p.S, p.G)
-                                      : (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + tab_bytes(p.G);
+    p.smem = (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + tab_bytes(p.G);
   if (p.smem > 227 * 1024) {
     if (err) *err = "bit-layout plan exceeds shared memory";
     return -1;

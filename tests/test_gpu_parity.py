@@ -385,23 +385,6 @@ def test_checkpoint_resume_is_bit_identical(layout):
     np.testing.assert_array_equal(a.observables()["acc"] + b.observables()["acc"], ref.observables()["acc"])
 
 
-@pytest.mark.parametrize("kind", [BIM, GAU])
-def test_warp_specialised_variant_matches(kind, monkeypatch):
-    """The producer/consumer variant (launch shape 4,4,4,768) takes the same decisions."""
-    L, R = 64, 8
-    temps = inputs.geometric_temps(1.0, 5.0, R)
-    ref = rf.Realization(L, temps, field_kind=kind, h=1.2, layout=BP)
-    monkeypatch.setenv("RFIM_BITS_PLAN", "4,4,4,768")
-    ws = rf.Realization(L, temps, field_kind=kind, h=1.2, layout=BP)
-    monkeypatch.delenv("RFIM_BITS_PLAN")
-    for g in (ref, ws):
-        g.run(20, 5, 0)
-    a, b = ref.get_state(), ws.get_state()
-    np.testing.assert_array_equal(a["spins"], b["spins"])
-    np.testing.assert_array_equal(a["t2r"], b["t2r"])
-    np.testing.assert_array_equal(ref.observables()["sums"], ws.observables()["sums"])
-
-
 @pytest.mark.parametrize("L,R,plan", [(64, 6, "0,4,4,512"), (64, 70, "0,4,4,512"), (32, 64, "0,4,4,512"),
                                        (64, 6, "0,4,1,512"), (64, 70, "0,4,1,512"), (32, 64, "0,4,1,384"),
                                        (64, 70, "0,4,2,896"), (64, 13, "0,4,2,896"), (64, 70, "0,8,8,512"),
