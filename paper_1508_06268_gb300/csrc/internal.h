@@ -47,6 +47,11 @@ struct RealView {
 // rfim_api.cu: records msg as the calling thread's last error (rfim_last_error(NULL)); returns code
 int set_thread_error(int code, const std::string &msg);
 
+// kernels_bits.cu: raises a kernel's dynamic shared-memory limit on the current device to at least
+// `bytes`, never lowering it: contexts and servers with different shapes share the same kernels,
+// and a smaller limit set by a later one would make the earlier one's launches fail.
+cudaError_t raise_smem_limit(const void *fn, size_t bytes);
+
 // host_tables.cu: bimodal thresholds (thr - 1, 32 entries per temperature), b2 = 2 beta,
 // b2l = -2 beta log2 e, beta = 1/T, gjn[u] = J (2u - 6)
 void bimodal_row(double beta, float J, float h, uint32_t out[32]);

@@ -79,7 +79,7 @@ int batch_max_gt(int L) { return (L == 64 || L == 32) ? 2 : 1; }
 size_t batch_smem(int L, int G) { return (size_t)G * 2 * ((size_t)L * L * L / 64) * 4 + tab_bytes(G); }
 
 cudaError_t batch_prepare(size_t smem) {
-  return cudaFuncSetAttribute((const void *)k_batch_bits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return raise_smem_limit((const void *)k_batch_bits, smem);
 }
 
 cudaError_t batch_occupancy(size_t smem, int *blocks_per_sm) {

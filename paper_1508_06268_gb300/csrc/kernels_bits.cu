@@ -16,6 +16,19 @@
 
 namespace rfim {
 
+cudaError_t raise_smem_limit(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> limit;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t &cur = limit[{dev, fn}];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 namespace {
 
 using KernelFn = void (*)(RealView, int32_t, uint32_t, int32_t, const float4 *, ExchArgs);
@@ -27,8 +40,10 @@ KernelFn pick(bool bim) {
 
 // Instances available to launch plans (L, cluster size S, replicas per thread GT, threads NT);
 // i8: the int8-layout staging instances (kernels_bits_i8.cu), default shapes only.
-KernelFn kernel_for(int L, int S, int GT, int NT, bool bim, bool i8 = false) {
-  if (i8) return (KernelFn)kernel_for_i8(L, S, GT, NT, bim);
+KernelFn kernel_for(int L, int S, int GT, int NT, bool bim, bool i8 = false, int ns = 1) {
+  if (i8) return ns == 1 ? (KernelFn)kernel_for_i8(L, S, GT, NT, bim) : nullptr;
+  if (ns == 4) return (KernelFn)kernel_for_split(L, S, GT, NT, bim);
+  if (ns != 1) return nullptr;
 #define RFIM_BITS_INSTANCE(l, s_, gt, nt) \
   if (L == l && S == s_ && GT == gt && NT == nt) return pick<l, s_, gt, nt>(bim);
   RFIM_BITS_INSTANCE(64, 1, 1, 512)
@@ -164,7 +179,7 @@ cudaError_t prepare_multihit(const BitsPlan &plan, bool bimodal) {
     if (!multihit_tile_ok(plan.L, T)) continue;
     MhFn fn = mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, bimodal, T);
     if (!fn) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    cudaError_t e = raise_smem_limit((const void *)fn, plan.smem);
     if (e == cudaSuccess && plan.S > 1)
       e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -188,9 +203,11 @@ void remember_tuned_plan(int32_t L, int32_t R, bool bimodal, const std::string &
 std::vector<std::string> plan_candidates(int32_t L) {
   if (L == 64)
     return {"4,4,4,512", "0,4,4,512", "0,4,1,512", "4,4,2,512", "2,2,2,512", "4,4,4,1024", "1,1,1,1024"};
-  if (L == 32) return {"2,1,1,256", "4,1,1,128", "1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512", "0,4,1,512"};
-  if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512"};
-  return {"1,16,1,128", "1,16,1,512", "1,8,1,128"};
+  if (L == 32)
+    return {"2,1,1,256", "4,1,1,128", "1,1,1,512", "1,2,2,512", "2,1,1,512", "0,4,4,512", "0,4,1,512",
+            "2,1,1,1024,4", "2,1,1,512,4", "4,1,1,512,4"};
+  if (L == 16) return {"1,8,1,512", "1,4,1,512", "1,16,1,512", "1,8,1,1024,4", "1,4,1,512,4", "1,8,1,512,4"};
+  return {"1,16,1,128", "1,16,1,512", "1,8,1,128", "1,16,1,512,4", "1,8,1,256,4"};
 }
 
 int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err, bool i8) {
@@ -213,7 +230,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
       KernelFn cf = kernel_for(L, 4, 4, 512, bimodal);
       const size_t smem = (size_t)4 * 2 * words_per_cta(L, 4) * 4 + tab_bytes(4);
       int maxc = 0;
-      if (cf && cudaFuncSetAttribute((const void *)cf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+      if (cf && raise_smem_limit((const void *)cf, smem) ==
                     cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)cluster_ctas);
@@ -232,12 +249,20 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
       grid = maxc > 0 && cluster_ctas > 4 * maxc;
     }
     if (grid) p.S = 0;
-  } else if (L == 32) {
+  } else if (L == 32 && i8) {
     p.S = 2; p.G = 1; p.GT = 1; p.threads = 256;  // two z slabs per replica, one word per thread
-  } else if (L == 16) {
+  } else if (L == 16 && i8) {
     p.S = 1; p.G = 8; p.GT = 1; p.threads = 512;
-  } else {
+  } else if (i8) {
     p.S = 1; p.G = 16; p.GT = 1; p.threads = 128;
+  } else if (L == 32) {
+    // four z slabs per replica, every word split over four warps (C3: 408 against 390 attempts/ns
+    // for two slabs of one word per thread)
+    p.S = 4; p.G = 1; p.GT = 1; p.threads = 512; p.NS = 4;
+  } else if (L == 16) {
+    p.S = 1; p.G = 4; p.GT = 1; p.threads = 512; p.NS = 4;  // C2: 23.3 against 16.7
+  } else {
+    p.S = 1; p.G = 4; p.GT = 1; p.threads = 512; p.NS = 4;  // C1: 3.1 against 1.5
   }
   // "S,G,GT,threads": the tuner's current candidate, else a tuned shape for this (L, R, field),
   // else the RFIM_BITS_PLAN environment override, else the defaults above
@@ -249,14 +274,17 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   }
   const char *o = t_plan_override ? t_plan_override : (!tuned.empty() ? tuned.c_str() : getenv("RFIM_BITS_PLAN"));
   if (o) {
-    int s, g, gt, th;
-    // an override that names no instance for this L (e.g. an L=64 shape while building L=16) is
-    // ignored and the defaults stand
-    const bool named = sscanf(o, "%d,%d,%d,%d", &s, &g, &gt, &th) == 4;
-    const bool exists = named && (s == 0 ? (!i8 && th >= 256 && th <= 1024 && th % 32 == 0 && grid_kernel_for(L, g, gt, th, bimodal))
-                                         : kernel_for(L, s, gt, th, bimodal, i8) != nullptr);
+    int s, g, gt, th, ns = 1;
+    // "S,G,GT,threads[,NS]" (NS = 4: every word split over four warps); an override that names no
+    // instance for this L (e.g. an L=64 shape while building L=16) is ignored and the defaults stand
+    const int nf = sscanf(o, "%d,%d,%d,%d,%d", &s, &g, &gt, &th, &ns);
+    const bool named = nf == 4 || nf == 5;
+    if (nf == 4) ns = 1;
+    const bool exists = named && (s == 0 ? (!i8 && ns == 1 && th >= 256 && th <= 1024 && th % 32 == 0 &&
+                                            grid_kernel_for(L, g, gt, th, bimodal))
+                                         : kernel_for(L, s, gt, th, bimodal, i8, ns) != nullptr);
     if (exists) {
-      p.S = s; p.G = g; p.GT = gt; p.threads = th;
+      p.S = s; p.G = g; p.GT = gt; p.threads = th; p.NS = ns;
     }
   }
   if (p.S != 0) {
@@ -266,7 +294,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal, i8);
+  KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal, i8, p.NS);
   GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.G, p.GT, p.threads, bimodal) : nullptr;
   if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
@@ -293,7 +321,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     return -1;
   }
   const void *fptr = gfn ? (const void *)gfn : (const void *)fn;
-  cudaError_t e = cudaFuncSetAttribute(fptr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  cudaError_t e = raise_smem_limit(fptr, p.smem);
   if (e == cudaSuccess && p.S > 1)
     e = cudaFuncSetAttribute(fptr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) {
@@ -398,7 +426,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   }
   const bool multihit = mh && mh->mh > 0;
   if (multihit && plan.S == 0) return cudaErrorInvalidConfiguration;
-  KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, plan.i8);
+  KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, plan.i8, plan.NS);
   MhFn mfn = multihit ? mh_kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, mh->tile) : nullptr;
   if (!fn && !mfn) return cudaErrorInvalidConfiguration;
   const int clusters = (v.R + plan.G - 1) / plan.G;

@@ -560,12 +560,51 @@ __device__ __forceinline__ void copy_slab(const RealView &v, uint32_t *sp, int r
   }
 }
 
+// Block pair BG (blocks 2 BG and 2 BG + 1) of word wl of replica g (one replica per unit): the
+// counts of the whole word, two Philox blocks and their decisions, and the flips xored into the
+// word in shared memory.  The four block pairs of a word are run by four warps; they flip disjoint
+// bits, and a pair's decisions read only its own bits of the word, so the order of their xors
+// does not matter.
+template <int L, int S, bool BIM, int BG>
+__device__ __forceinline__ void split_unit(const RealView &v, uint32_t *sp, int c, int g, int wl, int z0, int r0,
+                                           uint32_t sweep, uint32_t tag, uint32_t slot, const float4 *__restrict__ field4,
+                                           int up_rank, int dn_rank) {
+  using Gm = BitsGeom<L>;
+  constexpr int P = Gm::P, W = Gm::W, PZ = L / S, WC = PZ * P;
+  constexpr int64_t WPAD = (W + 31) / 32 * 32;
+  const int zl = wl / P, iw = wl % P, z = z0 + zl;
+  const int64_t wq = (int64_t)z * P + iw;
+  float4 h[2] = {};
+  if (!BIM) {
+    h[0] = __ldg(field4 + field4_index(c, wq, 2 * BG, WPAD));
+    h[1] = __ldg(field4 + field4_index(c, wq, 2 * BG + 1, WPAD));
+  }
+  uint32_t nb[6], c0, c1, c2;
+  neighbour_words<L, S>(sp + ((size_t)g * 2 + (c ^ 1)) * WC, zl, iw, parity0_mask<L>(c, z, iw), up_rank, dn_rank, nb);
+  count6(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], c0, c1, c2);
+  uint32_t *self = sp + ((size_t)g * 2 + c) * WC + wl;
+  const uint32_t fb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+  const PairSlices ps = make_pairs(c0, c1, c2, *self, fb);
+  uint32_t flip = 0u, fk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj) {  // block 2 BG + 1, then 2 BG: the sign collectors end with block 2 BG at bit 0
+    const int j = 2 * BG + 1 - jj;
+    const Words4 w = philox10(v.seed, v.realization, (uint32_t)(8 * wq + j), (uint32_t)(r0 + g), sweep, tag);
+    decide_block<BIM>(w, ps, j, slot, h[1 - jj], flip, fk);
+  }
+  if (!BIM) flip = (fk[0] | (fk[1] << 8) | (fk[2] << 16) | (fk[3] << 24)) << (2 * BG);
+  atomicXor(self, flip);
+}
+
 // One exchange interval of replicas [r0, r0 + gact) of realization v, slab `rank` of S: load into
 // shared memory, nsw sweeps, write back, and (xa.enabled) the energy partials and the exchange
 // tail.  All threads of the CTA call it; blockDim.x threads, dynamic shared memory >= the plan's.
 // I8: the realization is stored in the int8 layout (v.spins8) and staged here as bits: the slab is
 // packed into shared memory on entry and unpacked back on exit (a word is 32 consecutive bytes).
-template <int L, int S, int GT, bool BIM, bool XI = false, bool I8 = false>
+// NS = 4 (with GT = 1): every word is updated by four warps, one block pair each (split_unit), so
+// that small lattices, whose half-sweeps are too short to fill the SMs, run four times as many
+// threads with a quarter of the Philox work each.
+template <int L, int S, int GT, bool BIM, bool XI = false, bool I8 = false, int NS = 1>
 __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, int gact, int rank, uint32_t sweep0,
                                               int nsw, const float4 *__restrict__ field4, const ExchArgs &xa) {
   using Gm = BitsGeom<L>;
@@ -606,6 +645,24 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
       // the word update is written out here rather than called through update_word (which the
       // multi-hit kernel uses): the call changes the register allocation of this kernel (100 ->
       // 128 registers with spills for the float field at L = 64)
+      if constexpr (NS == 4) {
+        static_assert(GT == 1, "split words: one replica per unit");
+        const int warp = tid >> 5, bg = warp & 3, quads = nt >> 7;
+#pragma unroll 1
+        for (int item = (warp >> 2) * 32 + (tid & 31); ok && item < items; item += quads * 32) {
+          const int wl = item % WC, g = item / WC;
+          if (!RFIM_DCHECK(xa.err, g < gact && wl < WC, kDbgLattice)) continue;
+          const uint32_t slot = slot0 + (uint32_t)g * kTabSlot;
+          switch (bg) {  // warp-uniform
+            case 0: split_unit<L, S, BIM, 0>(v, sp, c, g, wl, z0, r0, sweep, tag, slot, field4, up_rank, dn_rank); break;
+            case 1: split_unit<L, S, BIM, 1>(v, sp, c, g, wl, z0, r0, sweep, tag, slot, field4, up_rank, dn_rank); break;
+            case 2: split_unit<L, S, BIM, 2>(v, sp, c, g, wl, z0, r0, sweep, tag, slot, field4, up_rank, dn_rank); break;
+            default: split_unit<L, S, BIM, 3>(v, sp, c, g, wl, z0, r0, sweep, tag, slot, field4, up_rank, dn_rank); break;
+          }
+        }
+        sync_slabs<S>();
+        continue;
+      }
 #pragma unroll 1
       for (int item = tid; ok && item < items; item += nt) {
         const int wl = item % WC, grp = item / WC;
@@ -676,14 +733,14 @@ __device__ __forceinline__ void bits_interval(const RealView &v, int G, int r0, 
   if (xa.enabled) interval_tail<L, S, BIM, XI>(v, G, r0, ok ? gact : 0, rank, nsw, field4, xa);
 }
 
-template <int L, int S, int GT, bool BIM, int NT, bool I8 = false>
+template <int L, int S, int GT, bool BIM, int NT, bool I8 = false, int NS = 1>
 __global__ void __launch_bounds__(NT) k_sweeps_bits(RealView v, int32_t G, uint32_t sweep0, int32_t nsw,
                                                      const float4 *__restrict__ field4, ExchArgs xa) {
   const int rank = S > 1 ? (int)cluster_rank() : 0;
   const int r0 = (int)(blockIdx.x / S) * G;
   const int gact = min(G, v.R - r0);
   xa.expected = gridDim.x;
-  bits_interval<L, S, GT, BIM, false, I8>(v, G, r0, gact, rank, sweep0, nsw, field4, xa);
+  bits_interval<L, S, GT, BIM, false, I8, NS>(v, G, r0, gact, rank, sweep0, nsw, field4, xa);
 }
 
 }  // namespace rfim

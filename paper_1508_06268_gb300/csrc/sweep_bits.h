@@ -29,6 +29,7 @@ struct BitsPlan {
   unsigned int *prog = nullptr;
   int32_t sms = 0;
   bool i8 = false;  // the realization is stored in the int8 layout and staged as bits (cluster shapes)
+  int32_t NS = 1;   // 4: every word split over four warps, one block pair each (small lattices)
 };
 
 // Multi-hit double 3D checkerboard (Sec. 3.2, kernels_mh.cuh): mh local passes per tile visit
@@ -52,6 +53,8 @@ std::vector<std::string> plan_candidates(int32_t L);
 int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::string *err, bool i8 = false);
 // The int8-layout staging instance for a cluster shape (kernels_bits_i8.cu), or null.
 void *kernel_for_i8(int L, int S, int GT, int NT, bool bim);
+// The split-word instance (NS = 4, kernels_bits_split.cu) for a shape, or null.
+void *kernel_for_split(int L, int S, int GT, int NT, bool bim);
 bool bits_plan_fits(const BitsPlan &plan, int32_t R);
 cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st);
 void free_bits_plan(BitsPlan &plan);

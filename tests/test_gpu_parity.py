@@ -587,3 +587,28 @@ def test_multihit_full_size_bit_exact():
     o.run(2, 1, 0)
     assert_same_state(g, o, "multi-hit at full size")
     np.testing.assert_array_equal(g.observables()["sums"], o.observables())
+
+
+@pytest.mark.parametrize("L,R,plan", [(32, 6, "2,1,1,1024,4"), (32, 3, "4,1,1,512,4"), (16, 11, "1,8,1,1024,4"),
+                                       (16, 5, "1,4,1,512,4"), (8, 20, "1,16,1,512,4"), (8, 7, "1,8,1,256,4")])
+def test_split_word_plans_bit_exact(L, R, plan, monkeypatch):
+    """Small-lattice plans that split every word over four warps (one Philox block pair each,
+    flips xored into the word): bimodal spins, permutation and sums equal the oracle's, with
+    partial replica groups; Gaussian spins and permutation equal the default plan's."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    monkeypatch.setenv("RFIM_BITS_PLAN", plan)
+    g = rf.Realization(L, temps, h=1.5, field_kind=BIM, field_seed=3, seed=42, layout=BP)
+    field = inputs.gaussian_field(L, 31)
+    gs = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP, seed=5)
+    monkeypatch.delenv("RFIM_BITS_PLAN")
+    o = oracle.Oracle(L, temps, h=1.5, field_kind=oracle.FIELD_BIMODAL, field_seed=3, seed=42)
+    g.run(12, 3, 0)
+    o.run(12, 3, 0)
+    assert_same_state(g, o, f"split plan {plan}")
+    np.testing.assert_array_equal(g.observables()["sums"], o.observables())
+    ref = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP, seed=5)
+    for x in (gs, ref):
+        x.run(12, 3, 0)
+    a, b = gs.get_state(), ref.get_state()
+    np.testing.assert_array_equal(a["spins"], b["spins"])
+    np.testing.assert_array_equal(a["t2r"], b["t2r"])
