@@ -202,3 +202,18 @@ def test_invalid_batch_shapes_rejected(shapes):
     with pytest.raises(rf.RfimError) as e:
         rf.Server(mem_budget_bytes=16 << 20, max_slots=2, batch_shapes=shapes)
     assert e.value.code == rf.EINVAL
+
+
+def test_servers_of_different_shapes_coexist():
+    """The batched kernel is shared by all servers: creating a server with smaller shapes must not
+    shrink the shared-memory limit that an earlier server's captured launches need."""
+    big = rf.Server(mem_budget_bytes=64 << 20, max_slots=2, batch_shapes="64:4:2")
+    small = rf.Server(mem_budget_bytes=64 << 20, max_slots=2, batch_shapes="64:1:1,32:4:1,16:4:1,8:8:1")
+    try:
+        a = big.wait(submit(big, 64, 8, rf.FIELD_BIMODAL, 7))
+        b = small.wait(submit(small, 64, 8, rf.FIELD_BIMODAL, 7))
+        for key in ("sums", "att", "acc"):
+            np.testing.assert_array_equal(a[key], b[key])
+    finally:
+        big.close()
+        small.close()
