@@ -268,8 +268,8 @@ const char *rfim_server_last_error(const rfim_server *s);
 
 /* ---- Exchange step without device allocation ------------------------------------------------------
    The paper has no counterpart to this entry point; it exists for callers that cannot allocate
-   device memory: a framework or arena that owns all of the device memory, a latency-critical loop
-   in which cudaMalloc / cudaFree would synchronise the device, or code recorded into a CUDA graph.
+   device memory: a framework or arena that owns all of the device memory, or a latency-critical
+   loop in which cudaMalloc / cudaFree would synchronise the device.
    It computes every replica's energy (Eq. 1) from caller-owned buffers and takes exchange step j
    exactly as rfim_exchange does (Eq. 2, Sec. 3.3; measurement of Sec. 7 when j >= measure_from),
    enqueued on `stream`.  It allocates nothing: its scratch (partial sums per replica and z slab,

@@ -1,8 +1,8 @@
 // rfim_exchange_noalloc: the energy reduction and exchange step on caller-owned device buffers,
 // with its scratch (per-(replica, slab) partial sums and the arrival counter) in a file-scope
 // device array instead of memory the library allocates.  For callers that cannot allocate
-// device memory: a framework or arena that owns all of it, a latency-critical loop where
-// cudaMalloc / cudaFree would synchronise the device, or code recorded into a CUDA graph.
+// device memory: a framework or arena that owns all of it, or a latency-critical loop where
+// cudaMalloc / cudaFree would synchronise the device.
 //
 // The array is shared by every call on a device and keeps the last call's contents; calls that
 // overlap on the GPU (different streams, or host threads without ordering) race on it.  The

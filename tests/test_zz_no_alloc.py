@@ -1,8 +1,8 @@
 """rfim_exchange_noalloc -- the exchange step for callers that cannot allocate device memory.
 
 Such callers have all device memory owned by another allocator (a framework's pool, a fixed
-arena), sit on a latency-critical path where cudaMalloc / cudaFree would synchronise the device,
-or record their launches into a CUDA graph.  The entry point keeps its scratch in a static
+arena), or sit on a latency-critical path where cudaMalloc / cudaFree would synchronise the
+device.  The entry point keeps its scratch in a static
 device array; the caller passes every input and output.  Checked here against the allocating
 entry point (rfim_exchange on a context holding the same state) on two calls in a row:
 permutation, exchange counts and measurement counts exactly, energies and measurement sums to
