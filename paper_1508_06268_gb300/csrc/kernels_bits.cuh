@@ -217,6 +217,9 @@ __device__ __forceinline__ void neighbour_words(const uint32_t *O, int zl, int i
     nb[5] = S == 1 ? O[(PZ - 1) * P + iw] : dsmem_load(O + (PZ - 1) * P + iw, dn_rank);
 }
 
+// Replicas reduced together by the fused exchange tail.
+constexpr int kTailRB = 4;
+
 template <typename T>
 __device__ __forceinline__ T warp_reduce_sum(T x) {
 #pragma unroll
@@ -329,69 +332,88 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
   const int nt = blockDim.x, tid = threadIdx.x;
 
   // ---- energy partials of this slab (Eq. 1): B over colour-0 words x their six neighbour words,
-  // M over all words, field term exact integer (bimodal) or error-free float sum (Sum2) -------
-  __shared__ long long red_i[3][32];
-  __shared__ double red_d[32];
+  // M over all words, field term exact integer (bimodal) or error-free float sum (Sum2) per
+  // thread.  Up to kTailRB replicas at a time: each word's field is loaded once for all of them,
+  // and one barrier pair reduces them all (warp trees, then one warp per replica over the warps).
+  constexpr int RB = kTailRB;
+  __shared__ int red_i[3][RB][32];
+  __shared__ double red_d[RB][32];
   __shared__ int last_cta;
   const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
-  for (int g = 0; g < gact; ++g) {
-    long long b = 0, m = 0, fi = 0;
-    float fs = 0.f, fe = 0.f;
+  for (int g0 = 0; g0 < gact; g0 += RB) {
+    const int ng = min(RB, gact - g0);
+    int b[RB], m[RB], fi[RB];
+    float fs[RB], fe[RB];
+#pragma unroll
+    for (int gg = 0; gg < RB; ++gg) {
+      b[gg] = m[gg] = fi[gg] = 0;
+      fs[gg] = fe[gg] = 0.f;
+    }
     for (int t = tid; t < 2 * WC; t += nt) {
       const int c = t / WC, wl = t % WC;
       const int zl = wl / P, iw = wl % P, z = z0 + zl;
       const int64_t wq = (int64_t)z * P + iw;
-      const uint32_t self = sp[((size_t)g * 2 + c) * WC + wl];
-      m += 2 * __popc(self) - 32;
-      if (c == 0) {
-        uint32_t nb[6];
-        neighbour_words<L, S>(sp + ((size_t)g * 2 + 1) * WC, zl, iw, parity0_mask<L>(0, z, iw), up_rank, dn_rank, nb);
+      const uint32_t hb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+      uint32_t self[RB];
 #pragma unroll
-        for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nb[d]);
+      for (int gg = 0; gg < RB; ++gg) {
+        self[gg] = gg < ng ? sp[((size_t)(g0 + gg) * 2 + c) * WC + wl] : 0u;
+        if (gg >= ng) continue;
+        m[gg] += 2 * __popc(self[gg]) - 32;
+        if (c == 0) {
+          uint32_t nb[6];
+          neighbour_words<L, S>(sp + ((size_t)(g0 + gg) * 2 + 1) * WC, zl, iw, parity0_mask<L>(0, z, iw), up_rank,
+                                dn_rank, nb);
+#pragma unroll
+          for (int d = 0; d < 6; ++d) b[gg] += 32 - 2 * __popc(self[gg] ^ nb[d]);
+        }
+        if (BIM) fi[gg] += 32 - 2 * __popc(self[gg] ^ hb);
       }
-      if (BIM) {
-        fi += 32 - 2 * __popc(self ^ v.hbits[(int64_t)c * W + wq]);
-      } else {
+      if (!BIM) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
           const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float term = ((self >> (8 * k + j)) & 1u) ? hk[k] : -hk[k];
-            const float tsum = __fadd_rn(fs, term);
-            const float bp = __fsub_rn(tsum, fs);
-            fe = __fadd_rn(fe, __fadd_rn(__fsub_rn(fs, __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
-            fs = tsum;
+          for (int gg = 0; gg < RB; ++gg) {
+            if (gg >= ng) continue;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float term = ((self[gg] >> (8 * k + j)) & 1u) ? hk[k] : -hk[k];
+              const float tsum = __fadd_rn(fs[gg], term);
+              const float bp = __fsub_rn(tsum, fs[gg]);
+              fe[gg] = __fadd_rn(fe[gg], __fadd_rn(__fsub_rn(fs[gg], __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
+              fs[gg] = tsum;
+            }
           }
         }
       }
     }
-    b = warp_reduce_sum(b);
-    m = warp_reduce_sum(m);
-    fi = warp_reduce_sum(fi);
-    double fd = warp_reduce_sum((double)fs + (double)fe);
-    if (lane == 0) {
-      red_i[0][wid] = b;
-      red_i[1][wid] = m;
-      red_i[2][wid] = fi;
-      red_d[wid] = fd;
+#pragma unroll
+    for (int gg = 0; gg < RB; ++gg) {
+      const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]), tf = warp_reduce_sum(fi[gg]);
+      const double td = warp_reduce_sum((double)fs[gg] + (double)fe[gg]);
+      if (lane == 0) {
+        red_i[0][gg][wid] = tb;
+        red_i[1][gg][wid] = tm;
+        red_i[2][gg][wid] = tf;
+        red_d[gg][wid] = td;
+      }
     }
     __syncthreads();
-    if (tid == 0) {
-      long long tb = 0, tm = 0, tf = 0;
-      double td = 0.0;
-      for (int w = 0; w < nw; ++w) {
-        tb += red_i[0][w];
-        tm += red_i[1][w];
-        tf += red_i[2][w];
-        td += red_d[w];
+    if (wid < ng) {  // warp gg adds the warps' partials of replica g0 + gg
+      const int gg = wid;
+      const long long tb = warp_reduce_sum(lane < nw ? (long long)red_i[0][gg][lane] : 0LL);
+      const long long tm = warp_reduce_sum(lane < nw ? (long long)red_i[1][gg][lane] : 0LL);
+      const long long tf = warp_reduce_sum(lane < nw ? (long long)red_i[2][gg][lane] : 0LL);
+      const double td = warp_reduce_sum(lane < nw ? red_d[gg][lane] : 0.0);
+      if (lane == 0) {
+        const int64_t slot = (int64_t)(r0 + g0 + gg) * S + rank;
+        xa.partB[slot] = tb;
+        xa.partM[slot] = tm;
+        xa.partFi[slot] = tf;
+        xa.partF[slot] = td;
       }
-      const int64_t slot = (int64_t)(r0 + g) * S + rank;
-      xa.partB[slot] = tb;
-      xa.partM[slot] = tm;
-      xa.partFi[slot] = tf;
-      xa.partF[slot] = td;
     }
     __syncthreads();
   }
