@@ -157,6 +157,25 @@ __global__ void k_build_field4(RealView v, float4 *field4, int64_t wpad) {
   }
 }
 
+// Largest |hh_i| as float bits (non-negative floats order like their bits) into *fmax.
+__global__ void k_field_absmax(RealView v, unsigned *fmax) {
+  unsigned m = 0u;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < v.N; t += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(v.hh_c[t]) & 0x7FFFFFFFu);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(fmax, m);
+}
+
+// Quantum of the energy tail's split field: q = 2^(E - 18), E = floor(log2 max |hh|), so that
+// |hh| / q < 2^19 (and 2^-126 for a field that is zero or subnormal).
+__global__ void k_field_quantum(float *fq, const unsigned *fmax) {
+  const unsigned mb = *fmax;
+  const int E = (int)(mb >> 23) - 127;
+  const int qe = mb < 0x00800000u ? -126 : max(E - 18, -126);
+  *fq = __uint_as_float((unsigned)(qe + 127) << 23);
+}
+
 }  // namespace
 
 bool bits_supported(int32_t L) { return L == 8 || L == 16 || L == 32 || L == 64; }
@@ -342,6 +361,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!bimodal) {
     const int64_t W = (int64_t)L * L * L / 64, wpad = (W + 31) / 32 * 32;
     rc = grab((void **)&p.field4, sizeof(float4) * 2 * wpad * 8, "field4");
+    if (!rc) rc = grab((void **)&p.fq, 8, "field quantum");
   }
   const size_t parts = (size_t)Rcap * p.S;
   if (!rc) rc = grab((void **)&p.partB, parts * 8, "partials");
@@ -369,11 +389,12 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
 bool bits_plan_fits(const BitsPlan &plan, int32_t R) { return R <= plan.Rcap; }
 
 void free_bits_plan(BitsPlan &plan) {
-  void *ptrs[] = {plan.field4, plan.partB, plan.partM, plan.partFi, plan.partF, plan.counter,
-                  plan.gpartB,  plan.gpartM, plan.gpartFi, plan.gpartF, plan.prog};
+  void *ptrs[] = {plan.field4, plan.fq, plan.partB, plan.partM, plan.partFi, plan.partF,
+                  plan.counter, plan.gpartB, plan.gpartM, plan.gpartFi, plan.gpartF, plan.prog};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   plan.field4 = nullptr;
+  plan.fq = nullptr;
   plan.partB = plan.partM = plan.partFi = nullptr;
   plan.partF = nullptr;
   plan.counter = nullptr;
@@ -386,6 +407,13 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
   if (!plan.field4) return cudaSuccess;
   const int64_t W = (int64_t)v.N / 64, wpad = (W + 31) / 32 * 32;
   k_build_field4<<<(int)((2 * W * 8 + 255) / 256), 256, 0, st>>>(v, plan.field4, wpad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !plan.fq) return e;
+  unsigned *fmax = reinterpret_cast<unsigned *>(plan.fq + 1);
+  e = cudaMemsetAsync(fmax, 0, 4, st);
+  if (e != cudaSuccess) return e;
+  k_field_absmax<<<152, 256, 0, st>>>(v, fmax);
+  k_field_quantum<<<1, 1, 0, st>>>(plan.fq, fmax);
   return cudaGetLastError();
 }
 
@@ -406,6 +434,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.expected = 0;  // set by the kernel to its grid size
   xa.ctl = nullptr;
   xa.err = plan.counter + 1;
+  xa.fq = plan.fq;
   if (plan.S == 0) {
     GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;

@@ -60,6 +60,9 @@ struct ExchArgs {
   // cos / sin(K t) tables [L], per-replica F of this interval [R], sums per temperature [R]
   const double *kcos, *ksin;
   double *Fr, *sumF;
+  // quantum q of the energy tail's split field (null: error-free float sums of hh instead): a
+  // power of two with |hh| / q < 2^19, so that the signed sum of a word's rint(hh / q) is exact
+  const float *fq;
 };
 
 __host__ __device__ __forceinline__ int64_t field4_index(int c, int64_t wq, int j, int64_t wpad) {
@@ -340,14 +343,17 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
   __shared__ double red_d[RB][32];
   __shared__ int last_cta;
   const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+  const float fq_f = (!BIM && xa.fq) ? *xa.fq : 1.0f, fq_inv = __frcp_rn(fq_f);  // fq: a power of two
   for (int g0 = 0; g0 < gact; g0 += RB) {
     const int ng = min(RB, gact - g0);
     int b[RB], m[RB], fi[RB];
     float fs[RB], fe[RB];
+    long long hint[RB];
 #pragma unroll
     for (int gg = 0; gg < RB; ++gg) {
       b[gg] = m[gg] = fi[gg] = 0;
       fs[gg] = fe[gg] = 0.f;
+      hint[gg] = 0;
     }
     for (int t = tid; t < 2 * WC; t += nt) {
       const int c = t / WC, wl = t % WC;
@@ -369,7 +375,37 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
         }
         if (BIM) fi[gg] += 32 - 2 * __popc(self[gg] ^ hb);
       }
-      if (!BIM) {
+      if (!BIM && xa.fq) {
+        // split field: hh = q hi + lo with hi = rint(hh / q) (|hi| < 2^19) and lo exact; the signed
+        // hi of a word summed exactly in float and carried in an integer (hint), the small lo
+        // summed in float (fe)
+        float wh[RB];
+#pragma unroll
+        for (int gg = 0; gg < RB; ++gg) wh[gg] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
+          const float hh[4] = {q4.x, q4.y, q4.z, q4.w};
+          float hk[4], lk[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            hk[k] = rintf(__fmul_rn(hh[k], fq_inv));     // scaling by a power of two: exact
+            lk[k] = __fmaf_rn(-hk[k], fq_f, hh[k]);      // exact remainder
+          }
+#pragma unroll
+          for (int gg = 0; gg < RB; ++gg) {
+            if (gg >= ng) continue;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float sgn = ((self[gg] >> (8 * k + j)) & 1u) ? 1.0f : -1.0f;
+              wh[gg] = __fmaf_rn(sgn, hk[k], wh[gg]);
+              fe[gg] = __fmaf_rn(sgn, lk[k], fe[gg]);
+            }
+          }
+        }
+#pragma unroll
+        for (int gg = 0; gg < RB; ++gg) hint[gg] += (long long)__float2int_rn(wh[gg]);
+      } else if (!BIM) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
@@ -392,7 +428,8 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
 #pragma unroll
     for (int gg = 0; gg < RB; ++gg) {
       const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]), tf = warp_reduce_sum(fi[gg]);
-      const double td = warp_reduce_sum((double)fs[gg] + (double)fe[gg]);
+      const double fq = (!BIM && xa.fq) ? (double)fq_f : 0.0;
+      const double td = warp_reduce_sum((double)fs[gg] + (double)fe[gg] + fq * (double)hint[gg]);
       if (lane == 0) {
         red_i[0][gg][wid] = tb;
         red_i[1][gg][wid] = tm;

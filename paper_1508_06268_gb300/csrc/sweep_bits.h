@@ -19,6 +19,7 @@ struct BitsPlan {
   size_t smem = 0;
   int32_t Rcap = 0;
   float4 *field4 = nullptr;  // float path: hh as float4 per (colour, word, chunk), see kernels_bits.cu
+  float *fq = nullptr;       // float path: [0] quantum of the energy tail's split field, [1] max |hh| bits
   // fused exchange tail: per-(replica, slab) partials and the arrival counter
   long long *partB = nullptr, *partM = nullptr, *partFi = nullptr;
   double *partF = nullptr;
