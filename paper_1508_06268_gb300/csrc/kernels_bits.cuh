@@ -220,8 +220,14 @@ __device__ __forceinline__ void neighbour_words(const uint32_t *O, int zl, int i
     nb[5] = S == 1 ? O[(PZ - 1) * P + iw] : dsmem_load(O + (PZ - 1) * P + iw, dn_rank);
 }
 
-// Replicas reduced together by the fused exchange tail.
+// Replicas reduced together by the fused exchange tail.  Every L = 32 launch shape holds at most
+// two replicas per CTA, and there, with a float field, the four-replica tail's registers slowed
+// the sweeps themselves (L = 32, R = 70: 49.8 -> 55.5 us per 10 sweeps), so that case reduces
+// one replica at a time (with the bimodal field four stays faster: 53.4 against 56.9 us per
+// interval).
 constexpr int kTailRB = 4;
+template <int L, bool BIM>
+constexpr int tail_rb() { return (L == 32 && !BIM) ? 1 : kTailRB; }
 
 template <typename T>
 __device__ __forceinline__ T warp_reduce_sum(T x) {
@@ -322,7 +328,7 @@ __device__ __forceinline__ void xi_replicas(const uint32_t *sp, int r0, int gact
 // xa.j): slab partials of each replica from the lattice still in shared memory, an arrival count,
 // and for the last arrival the ordered reduction, E = -J B - F, exchange and measurement.  XI
 // (whole replicas, S = 1): on measuring steps with xa.sumF set, also the structure factor.
-template <int L, int S, bool BIM, bool XI = false>
+template <int L, int S, bool BIM, bool XI = false, int RB = tail_rb<L, BIM>()>
 __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, int gact, int rank, int nsw,
                                               const float4 *__restrict__ field4, const ExchArgs &xa) {
   using Gm = BitsGeom<L>;
@@ -335,10 +341,9 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
   const int nt = blockDim.x, tid = threadIdx.x;
 
   // ---- energy partials of this slab (Eq. 1): B over colour-0 words x their six neighbour words,
-  // M over all words, field term exact integer (bimodal) or error-free float sum (Sum2) per
-  // thread.  Up to kTailRB replicas at a time: each word's field is loaded once for all of them,
+  // M over all words, field term exact integer (bimodal), else the split sum below (or, with no
+  // quantum given, an error-free float sum, Sum2) per thread.  Up to RB replicas at a time: each word's field is loaded once for all of them,
   // and one barrier pair reduces them all (warp trees, then one warp per replica over the warps).
-  constexpr int RB = kTailRB;
   __shared__ int red_i[3][RB][32];
   __shared__ double red_d[RB][32];
   __shared__ int last_cta;
