@@ -167,13 +167,36 @@ __global__ void k_field_absmax(RealView v, unsigned *fmax) {
   if ((threadIdx.x & 31) == 0) atomicMax(fmax, m);
 }
 
-// Quantum of the energy tail's split field: q = 2^(E - 18), E = floor(log2 max |hh|), so that
-// |hh| / q < 2^19 (and 2^-126 for a field that is zero or subnormal).
-__global__ void k_field_quantum(float *fq, const unsigned *fmax) {
-  const unsigned mb = *fmax;
-  const int E = (int)(mb >> 23) - 127;
-  const int qe = mb < 0x00800000u ? -126 : max(E - 18, -126);
-  *fq = __uint_as_float((unsigned)(qe + 127) << 23);
+// Fixed-point field of the energy tail: qe = E - 38 with E = floor(log2 max |hh|) (-127 when the
+// maximum is zero or subnormal), so |hh| / 2^qe < 2^39.  H = rint(hh / 2^qe) is exact wherever hh
+// is at least 2^(qe + 23) and rounded by at most 2^(qe - 1) below; one thread per four sites
+// (colour, word, block j) writes their five byte limbs, and the lattice sum of H goes to Htot.
+__global__ void k_field_limbs(RealView v, uint4 *flimb, FieldQuant *fz, int64_t wpad) {
+  const unsigned mb = fz->fmax;
+  const int E = mb < 0x00800000u ? -127 : (int)(mb >> 23) - 127;
+  const int qe = E - 38;
+  const int64_t half = (int64_t)v.N / 2, W = half / 32;
+  long long hsum = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * W * 8; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / (W * 8));
+    const int64_t wq = (t / 8) % W;
+    const int j = (int)(t % 8);
+    const float *h = v.hh_c + c * half + wq * 32 + 4 * j;
+    uint32_t lo[4] = {0u, 0u, 0u, 0u}, top = 0u;
+    for (int k = 0; k < 4; ++k) {
+      const long long H = llrint(ldexp((double)h[k], -qe));
+      hsum += H;
+      const unsigned long long u = (unsigned long long)H;
+      for (int l = 0; l < 4; ++l) lo[l] |= (uint32_t)((u >> (8 * l)) & 0xFFu) << (8 * k);
+      top |= (uint32_t)((u >> 32) & 0xFFu) << (8 * k);  // two's complement: floor(H / 2^32) as a byte
+    }
+    flimb[flimb_index(c, wq, j, wpad)] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    reinterpret_cast<uint32_t *>(flimb + flimb_index(c, wq, 8 + j / 4, wpad))[j % 4] = top;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&fz->Htot), (unsigned long long)hsum);
+  if (blockIdx.x == 0 && threadIdx.x == 0) fz->qe = qe;
 }
 
 }  // namespace
@@ -361,7 +384,8 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!bimodal) {
     const int64_t W = (int64_t)L * L * L / 64, wpad = (W + 31) / 32 * 32;
     rc = grab((void **)&p.field4, sizeof(float4) * 2 * wpad * 8, "field4");
-    if (!rc) rc = grab((void **)&p.fq, 8, "field quantum");
+    if (!rc) rc = grab((void **)&p.flimb, sizeof(uint4) * 2 * 10 * wpad, "field limbs");
+    if (!rc) rc = grab((void **)&p.fquant, sizeof(FieldQuant), "field quantum");
   }
   const size_t parts = (size_t)Rcap * p.S;
   if (!rc) rc = grab((void **)&p.partB, parts * 8, "partials");
@@ -389,12 +413,13 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
 bool bits_plan_fits(const BitsPlan &plan, int32_t R) { return R <= plan.Rcap; }
 
 void free_bits_plan(BitsPlan &plan) {
-  void *ptrs[] = {plan.field4, plan.fq, plan.partB, plan.partM, plan.partFi, plan.partF,
+  void *ptrs[] = {plan.field4, plan.flimb, plan.fquant, plan.partB, plan.partM, plan.partFi, plan.partF,
                   plan.counter, plan.gpartB, plan.gpartM, plan.gpartFi, plan.gpartF, plan.prog};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   plan.field4 = nullptr;
-  plan.fq = nullptr;
+  plan.flimb = nullptr;
+  plan.fquant = nullptr;
   plan.partB = plan.partM = plan.partFi = nullptr;
   plan.partF = nullptr;
   plan.counter = nullptr;
@@ -408,12 +433,11 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
   const int64_t W = (int64_t)v.N / 64, wpad = (W + 31) / 32 * 32;
   k_build_field4<<<(int)((2 * W * 8 + 255) / 256), 256, 0, st>>>(v, plan.field4, wpad);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !plan.fq) return e;
-  unsigned *fmax = reinterpret_cast<unsigned *>(plan.fq + 1);
-  e = cudaMemsetAsync(fmax, 0, 4, st);
+  if (e != cudaSuccess || !plan.flimb || !plan.fquant) return e;
+  e = cudaMemsetAsync(plan.fquant, 0, sizeof(FieldQuant), st);
   if (e != cudaSuccess) return e;
-  k_field_absmax<<<152, 256, 0, st>>>(v, fmax);
-  k_field_quantum<<<1, 1, 0, st>>>(plan.fq, fmax);
+  k_field_absmax<<<152, 256, 0, st>>>(v, &plan.fquant->fmax);
+  k_field_limbs<<<(int)std::min<int64_t>((2 * W * 8 + 255) / 256, 4 * 152), 256, 0, st>>>(v, plan.flimb, plan.fquant, wpad);
   return cudaGetLastError();
 }
 
@@ -434,7 +458,8 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.expected = 0;  // set by the kernel to its grid size
   xa.ctl = nullptr;
   xa.err = plan.counter + 1;
-  xa.fq = plan.fq;
+  xa.flimb = plan.flimb;
+  xa.fquant = plan.fquant;
   if (plan.S == 0) {
     GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;

@@ -45,6 +45,14 @@ struct SlotCtl {
 
 // Arguments of the fused exchange tail.  Partials are [Rcap][S]; counter is zero between launches
 // and `expected` arrivals (CTAs or work items) complete the realization.
+// Fixed-point form of a float field for exact energy sums: H_i = rint(hh_i / 2^qe) with
+// |H_i| < 2^39, so that H_i is five bytes (four unsigned, the top one signed); Htot = sum_i H_i.
+struct FieldQuant {
+  long long Htot;
+  int qe;
+  unsigned fmax;  // largest |hh_i| as float bits (while building)
+};
+
 struct ExchArgs {
   int32_t enabled;
   uint32_t j;
@@ -60,13 +68,21 @@ struct ExchArgs {
   // cos / sin(K t) tables [L], per-replica F of this interval [R], sums per temperature [R]
   const double *kcos, *ksin;
   double *Fr, *sumF;
-  // quantum q of the energy tail's split field (null: error-free float sums of hh instead): a
-  // power of two with |hh| / q < 2^19, so that the signed sum of a word's rint(hh / q) is exact
-  const float *fq;
+  // fixed-point field of the energy tail (both null: error-free float sums of hh instead):
+  // H = rint(hh / q), q = 2^qe, as byte limbs (flimb_index) and the lattice sum of H
+  const uint4 *flimb;
+  const FieldQuant *fquant;
 };
 
 __host__ __device__ __forceinline__ int64_t field4_index(int c, int64_t wq, int j, int64_t wpad) {
   return ((int64_t)c * wpad + (wq & ~31LL)) * 8 + (int64_t)j * 32 + (wq & 31);
+}
+
+// uint4 s of colour c, word wq: s < 8, limbs 0..3 (.x .. .w) of the four sites 4s + k (byte k);
+// s = 8, 9: limb 4 of blocks 4(s - 8) .. 4(s - 8) + 3 (.x .. .w), each byte one site.  Words are
+// the fastest index, so a warp's loads of one s are contiguous.
+__host__ __device__ __forceinline__ int64_t flimb_index(int c, int64_t wq, int s, int64_t wpad) {
+  return ((int64_t)c * 10 + s) * wpad + wq;
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -341,24 +357,30 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
   const int nt = blockDim.x, tid = threadIdx.x;
 
   // ---- energy partials of this slab (Eq. 1): B over colour-0 words x their six neighbour words,
-  // M over all words, field term exact integer (bimodal), else the split sum below (or, with no
-  // quantum given, an error-free float sum, Sum2) per thread.  Up to RB replicas at a time: each word's field is loaded once for all of them,
-  // and one barrier pair reduces them all (warp trees, then one warp per replica over the warps).
-  __shared__ int red_i[3][RB][32];
+  // M over all words and the field term per thread, up to RB replicas at a time (each word's field
+  // is loaded once for all of them; one barrier pair reduces them all: warp trees, then one warp
+  // per replica over the warps).  Field term: bimodal, the exact integer sum of hb s; float field
+  // with the fixed-point limbs (xa.flimb), the exact integer sum of H over the up spins of the
+  // slab, H = rint(hh / q) in five byte limbs summed by four-way byte dot products against the
+  // spin bits of each Philox block (F = q (2 sum_up H - sum_all H) in the last CTA); without them,
+  // an error-free float sum (Sum2).
+  __shared__ int red_i[BIM ? 3 : 2][RB][32];
+  __shared__ long long red_l[BIM ? 1 : RB][32];
   __shared__ double red_d[RB][32];
   __shared__ int last_cta;
   const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
-  const float fq_f = (!BIM && xa.fq) ? *xa.fq : 1.0f, fq_inv = __frcp_rn(fq_f);  // fq: a power of two
+  const bool limbs = !BIM && xa.flimb != nullptr;
   for (int g0 = 0; g0 < gact; g0 += RB) {
     const int ng = min(RB, gact - g0);
-    int b[RB], m[RB], fi[RB];
+    int b[RB], m[RB], fi[RB], hs[RB];
+    unsigned hu[RB][4];
     float fs[RB], fe[RB];
-    long long hint[RB];
 #pragma unroll
     for (int gg = 0; gg < RB; ++gg) {
-      b[gg] = m[gg] = fi[gg] = 0;
+      b[gg] = m[gg] = fi[gg] = hs[gg] = 0;
       fs[gg] = fe[gg] = 0.f;
-      hint[gg] = 0;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) hu[gg][l] = 0u;
     }
     for (int t = tid; t < 2 * WC; t += nt) {
       const int c = t / WC, wl = t % WC;
@@ -380,36 +402,25 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
         }
         if (BIM) fi[gg] += 32 - 2 * __popc(self[gg] ^ hb);
       }
-      if (!BIM && xa.fq) {
-        // split field: hh = q hi + lo with hi = rint(hh / q) (|hi| < 2^19) and lo exact; the signed
-        // hi of a word summed exactly in float and carried in an integer (hint), the small lo
-        // summed in float (fe)
-        float wh[RB];
-#pragma unroll
-        for (int gg = 0; gg < RB; ++gg) wh[gg] = 0.f;
+      if (limbs) {
+        // block j: byte k of (self >> j) & 0x01010101 is the up bit of site 4j + k
+        const uint4 top0 = __ldg(xa.flimb + flimb_index(c, wq, 8, WPAD));
+        const uint4 top1 = __ldg(xa.flimb + flimb_index(c, wq, 9, WPAD));
+        const uint32_t top[8] = {top0.x, top0.y, top0.z, top0.w, top1.x, top1.y, top1.z, top1.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
-          const float hh[4] = {q4.x, q4.y, q4.z, q4.w};
-          float hk[4], lk[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            hk[k] = rintf(__fmul_rn(hh[k], fq_inv));     // scaling by a power of two: exact
-            lk[k] = __fmaf_rn(-hk[k], fq_f, hh[k]);      // exact remainder
-          }
+          const uint4 lo = __ldg(xa.flimb + flimb_index(c, wq, j, WPAD));
 #pragma unroll
           for (int gg = 0; gg < RB; ++gg) {
             if (gg >= ng) continue;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float sgn = ((self[gg] >> (8 * k + j)) & 1u) ? 1.0f : -1.0f;
-              wh[gg] = __fmaf_rn(sgn, hk[k], wh[gg]);
-              fe[gg] = __fmaf_rn(sgn, lk[k], fe[gg]);
-            }
+            const uint32_t up = (self[gg] >> j) & 0x01010101u;
+            hu[gg][0] = __dp4a(up, lo.x, hu[gg][0]);
+            hu[gg][1] = __dp4a(up, lo.y, hu[gg][1]);
+            hu[gg][2] = __dp4a(up, lo.z, hu[gg][2]);
+            hu[gg][3] = __dp4a(up, lo.w, hu[gg][3]);
+            hs[gg] = __dp4a((int)up, (int)top[j], hs[gg]);  // top limb signed, up bytes 0 or 1
           }
         }
-#pragma unroll
-        for (int gg = 0; gg < RB; ++gg) hint[gg] += (long long)__float2int_rn(wh[gg]);
       } else if (!BIM) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -432,13 +443,23 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
     }
 #pragma unroll
     for (int gg = 0; gg < RB; ++gg) {
-      const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]), tf = warp_reduce_sum(fi[gg]);
-      const double fq = (!BIM && xa.fq) ? (double)fq_f : 0.0;
-      const double td = warp_reduce_sum((double)fs[gg] + (double)fe[gg] + fq * (double)hint[gg]);
+      const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]);
+      // field integer: bimodal sum of hb s (int), or the up-spin sum of H from its limbs
+      if constexpr (BIM) {
+        const int tf = warp_reduce_sum(fi[gg]);
+        if (lane == 0) red_i[2][gg][wid] = tf;
+      } else {
+        long long fl = 0;
+        if (limbs)
+          fl = (long long)hu[gg][0] + ((long long)hu[gg][1] << 8) + ((long long)hu[gg][2] << 16) +
+               ((long long)hu[gg][3] << 24) + ((long long)hs[gg] << 32);
+        const long long tf = warp_reduce_sum(fl);
+        if (lane == 0) red_l[gg][wid] = tf;
+      }
+      const double td = (BIM || limbs) ? 0.0 : warp_reduce_sum((double)fs[gg] + (double)fe[gg]);
       if (lane == 0) {
         red_i[0][gg][wid] = tb;
         red_i[1][gg][wid] = tm;
-        red_i[2][gg][wid] = tf;
         red_d[gg][wid] = td;
       }
     }
@@ -447,7 +468,8 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
       const int gg = wid;
       const long long tb = warp_reduce_sum(lane < nw ? (long long)red_i[0][gg][lane] : 0LL);
       const long long tm = warp_reduce_sum(lane < nw ? (long long)red_i[1][gg][lane] : 0LL);
-      const long long tf = warp_reduce_sum(lane < nw ? (long long)red_i[2][gg][lane] : 0LL);
+      const long long tf =
+          warp_reduce_sum(lane < nw ? (BIM ? (long long)red_i[BIM ? 2 : 0][gg][lane] : red_l[BIM ? 0 : gg][lane]) : 0LL);
       const double td = warp_reduce_sum(lane < nw ? red_d[gg][lane] : 0.0);
       if (lane == 0) {
         const int64_t slot = (int64_t)(r0 + g0 + gg) * S + rank;
@@ -481,7 +503,8 @@ __device__ __forceinline__ void interval_tail(const RealView &v, int G, int r0, 
       tf += __ldcg(xa.partFi + slot);
       td += __ldcg(xa.partF + slot);
     }
-    const double F = BIM ? xa.h * (double)tf : td;
+    const double F = BIM ? xa.h * (double)tf
+                         : (xa.flimb ? ldexp((double)(2 * tf - xa.fquant->Htot), xa.fquant->qe) : td);
     v.E[r] = -xa.J * (double)tb - F;
     v.M[r] = tm;
   }

@@ -10,6 +10,8 @@
 
 namespace rfim {
 
+struct FieldQuant;  // kernels_bits.cuh
+
 // How one realization is mapped onto CTAs: a cluster of S CTAs (z slabs of L/S planes each)
 // holds G replicas; every thread updates a word of the slab for GT of them at once (so one field
 // load serves GT replicas).  Grid = ceil(R / G) clusters.  S == 0 selects the grid-wide
@@ -19,7 +21,9 @@ struct BitsPlan {
   size_t smem = 0;
   int32_t Rcap = 0;
   float4 *field4 = nullptr;  // float path: hh as float4 per (colour, word, chunk), see kernels_bits.cu
-  float *fq = nullptr;       // float path: [0] quantum of the energy tail's split field, [1] max |hh| bits
+  // float path: fixed-point field of the energy tail (flimb_index layout) and its exponent/sum
+  uint4 *flimb = nullptr;
+  FieldQuant *fquant = nullptr;
   // fused exchange tail: per-(replica, slab) partials and the arrival counter
   long long *partB = nullptr, *partM = nullptr, *partFi = nullptr;
   double *partF = nullptr;
