@@ -207,7 +207,7 @@ size_t slot_bytes(int32_t L, int32_t R, int32_t kind, bool xi) {
   auto add = [&](size_t x) { b += Arena::round(x); };
   add((size_t)R * 2 * W * 4);                         // bits
   add(2 * W * 4);                                     // hbits
-  if (kind != kBimodal) add(2 * wpad * 8 * 16);      // field4
+  if (kind != kBimodal) { add(2 * wpad * 8 * 16); add(2 * 10 * wpad * 16); add(sizeof(FieldQuant)); }  // field4, limbs
   add(N * 4); add(N * 4); add(N);                     // hraw, hh_c, hbit_c
   add((size_t)R * 32 * 4); add(32); add(R * 4); add(R * 4); add(R * 8);  // thr gjn b2 b2l beta
   add(R * 4); add(R * 4); add(R * 8); add(R * 8); add(R * 8); add(R * 8);  // t2r r2t E M att acc
@@ -234,6 +234,8 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
   v.bits = (uint32_t *)take((size_t)R * 2 * W * 4);
   uint32_t *hbits = (uint32_t *)take(2 * W * 4);
   float4 *field4 = c.field_kind != kBimodal ? (float4 *)take(2 * wpad * 8 * 16) : nullptr;
+  uint4 *flimb = field4 ? (uint4 *)take(2 * 10 * wpad * 16) : nullptr;
+  FieldQuant *fquant = field4 ? (FieldQuant *)take(sizeof(FieldQuant)) : nullptr;
   float *hraw = (float *)take(N * 4);
   float *hh_c = (float *)take(N * 4);
   uint8_t *hbit_c = (uint8_t *)take(N);
@@ -284,9 +286,15 @@ int init_slot(rfim_server *s, Slot &sl, const Request &rq) {
   if (field4) {
     BitsPlan tmp;
     tmp.field4 = field4;
+    tmp.flimb = flimb;
+    tmp.fquant = fquant;
     const cudaError_t e = build_field4(v, tmp, st);
     tmp.field4 = nullptr;  // owned by the arena
+    tmp.flimb = nullptr;
+    tmp.fquant = nullptr;
     if (!ck(e, "field4")) return RFIM_ECUDA;
+    xa.flimb = flimb;
+    xa.fquant = fquant;
   }
   if (!ck(launch_init_spins(v, R, 0, true, st), "init")) return RFIM_ECUDA;
   std::vector<uint32_t> thr_h((size_t)R * 32);

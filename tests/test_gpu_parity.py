@@ -180,6 +180,26 @@ def test_gaussian_energies_match():
     np.testing.assert_allclose(E, ref, rtol=1e-9, atol=1e-7)
 
 
+@pytest.mark.parametrize("L,R", [(8, 6), (16, 5), (32, 4), (64, 4)])
+def test_fused_tail_gaussian_energies_match_oracle(L, R):
+    """Eq. 1 energies as the fused exchange tail computes them for a float field (read back
+    through the one measurement of one exchange interval) equal the oracle's energies of the same
+    final spins to 1e-12 relative: the field term is summed exactly in fixed point."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 5)
+    g = rf.Realization(L, temps, field_kind=EXP, field=field, seed=7, layout=BP)
+    g.run(10, 10, 0)
+    st = g.get_state()
+    obs = g.observables()
+    g.close()
+    assert obs["n_meas"] == 1
+    sums = obs["sums"]
+    o = oracle.Oracle(L, temps, field_kind=EXP, field=field)
+    o.set_spins(st["spins"])
+    ref = np.array([o.energy(int(st["t2r"][k]))[0] for k in range(R)])
+    np.testing.assert_allclose(sums[:, 0] * L ** 3, ref, rtol=1e-12)
+
+
 def _binned(run, n_bins):
     """Bin means and their standard errors from n_bins + 1 cumulative readings of run() ->
     (obs sums [R][5], n_meas, att [R-1], acc [R-1]): per-temperature <e>, <e^2>, <|m|>, <m^2>,

@@ -95,8 +95,8 @@ def test_bimodal_served_equals_oracle(L, R, real):
 
 
 def test_admission_by_memory_budget():
-    # budget for two L=32, R=16 Gaussian realizations (about 0.5 MB each) at a time
-    with rf.Server(mem_budget_bytes=1_100_000, max_slots=8, intervals_per_launch=1) as srv:
+    # budget for two L=32, R=16 Gaussian realizations (about 0.67 MB each) at a time
+    with rf.Server(mem_budget_bytes=1_400_000, max_slots=8, intervals_per_launch=1) as srv:
         tickets = [submit(srv, 32, 16, rf.FIELD_GAUSSIAN, r, sweeps=20) for r in range(6)]
         peak = 0
         results = {}
