@@ -43,7 +43,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
 # (one exchange interval, 3.36e8 attempts, in either layout) from
 # one ncu capture of the current kernel version; None when the kernel changed since the capture.
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": None, "k_sweeps_bits (int8 layout staged as bits)": None}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6}
 
 
 def parse():
