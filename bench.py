@@ -43,7 +43,8 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
 # (one exchange interval, 3.36e8 attempts, in either layout) from
 # one ncu capture of the current kernel version; None when the kernel changed since the capture.
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6}
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.711296e6,
+                       "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6}
 
 
 def parse():
@@ -585,12 +586,13 @@ def measure_layout(rf, torch, layout, args, T, real, field_seed, local, dist):
     prof = g.profile_read()
     g.profile(False)
     launches = g.launch_count - launches0
+    plan = g.plan()
     g.close()
     del flush
     if dist is not None:
         dist.barrier()
     return {"dev_ms": max_over_ranks(dev_ms, dist, "cuda"), "dev_ms_local": dev_ms, "wall": wall, "prof": prof,
-            "launches": launches, "clk": clk}
+            "launches": launches, "clk": clk, "plan": plan}
 
 
 def roofline_of(m, layout, rf, props, steps):
@@ -601,11 +603,15 @@ def roofline_of(m, layout, rf, props, steps):
     achieved = L ** 3 * R * EX / (group_ms * 1e6)  # Gattempts/s
     sm_mhz = clk["sm_mhz"] or 2070.0
     peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
-    # the int8 layout at L = 64 runs the same kernel with its slabs staged from bytes into bits
-    kernel = "k_sweeps_bits" if layout == rf.LAYOUT_BITPACK else "k_sweeps_bits (int8 layout staged as bits)"
+    # the int8 layout at L = 64 runs the cluster kernel with its slabs staged from bytes into bits;
+    # the bit layout runs the grid-wide kernel when its plan says S = 0
+    if layout != rf.LAYOUT_BITPACK:
+        kernel = "k_sweeps_bits (int8 layout staged as bits)"
+    else:
+        kernel = "k_sweeps_grid" if m.get("plan", "").startswith("0,") else "k_sweeps_bits"
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s", "frac": achieved / peak,
             "traffic": SWEEP_TRAFFIC_BYTES.get(kernel), "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
-            "kernel": kernel,
+            "kernel": kernel, "plan": m.get("plan"),
             "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
                           f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
                           f"{sm_mhz:.0f} MHz (median sampled)",

@@ -325,6 +325,13 @@ int rfim_profile_read(rfim_ctx *ctx, double *sweep_ms, int64_t *sweep_launches, 
    scratch realizations.  Errors: RFIM_EINVAL (unsupported L, R < 2), RFIM_ECUDA. */
 int rfim_tune(int32_t L, int32_t R, int32_t field_kind, char *plan_out, int32_t plan_cap, double *attempts_per_ns);
 
+/* Launch shape of this context's sweep kernel, in the format rfim_tune reports: "S,G,GT,threads"
+   with ",4" appended when every word is split over four warps (S = 0: the grid-wide plan), and
+   ",int8" appended when the int8 layout is staged as bits; "" when the context runs the int8
+   kernels (L outside 8, 16, 32, 64).  plan_out receives at most plan_cap chars (NUL included).
+   Errors: RFIM_EINVAL (NULL ctx or plan_out, plan_cap < 1). */
+int rfim_get_plan(const rfim_ctx *ctx, char *plan_out, int32_t plan_cap);
+
 /* Host-only self-check of the bit layout's word-level neighbour arithmetic (multi-spin coding,
    Eq. 3 colours) against direct neighbour lookup on a random L^3 lattice; needs no GPU.
    Returns the number of mismatching sites (0 = pass) or -1 for an unsupported L. */

@@ -123,6 +123,7 @@ def load():
             L.rfim_tune.argtypes = [i32, i32, i32, C.c_char_p, i32, C.POINTER(C.c_double)]
             L.rfim_server_tune.argtypes = [C.POINTER(ServerTuneConfig), C.c_char_p, i32, C.POINTER(i32),
                                            C.POINTER(C.c_double)]
+            L.rfim_get_plan.argtypes = [P, C.c_char_p, i32]
             L.rfim_profile.argtypes = [P, C.c_int]
             L.rfim_profile_read.argtypes = [P, P, P, P, P]
             for name in ("rfim_create", "rfim_destroy", "rfim_sweep", "rfim_exchange", "rfim_run",
@@ -133,7 +134,7 @@ def load():
                          "rfim_exchange_noalloc", "rfim_tune", "rfim_selftest_grid", "rfim_selftest_wait",
                          "rfim_set_measure_xi", "rfim_set_multihit", "rfim_thermal",
                          "rfim_disorder_average", "rfim_server_tune", "rfim_debug_build",
-                         "rfim_selftest_debug"):
+                         "rfim_selftest_debug", "rfim_get_plan"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -361,6 +362,12 @@ class Realization:
         out = np.zeros(self.N, dtype=np.float32)
         self._check(self._lib.rfim_get_field(self._h, _ptr(out)))
         return out
+
+    def plan(self) -> str:
+        """Launch shape of the sweep kernel ("S,G,GT,threads[,4][,int8]"; "" for the int8 kernels)."""
+        buf = C.create_string_buffer(64)
+        self._check(self._lib.rfim_get_plan(self._h, buf, 64))
+        return buf.value.decode()
 
     def profile(self, enable=True):
         self._check(self._lib.rfim_profile(self._h, 1 if enable else 0))

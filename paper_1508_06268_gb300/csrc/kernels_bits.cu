@@ -267,7 +267,10 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     // second wave; 36 clusters of 4 at one CTA per SM on GB300); then the grid-wide plan
     const int cluster_ctas = 4 * ((Rcap + 3) / 4);
     p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;
-    bool grid = sms_dev > 0 && cluster_ctas < (4 * sms_dev) / 5;
+    // grid-wide plan when clusters of 4 would leave an eighth of the SMs or more idle (measured at
+    // L = 64, Gaussian field: R = 112 / 120 / 128 grid 945 / 954 / 999 against clusters 860 / 923 /
+    // 984 attempts/ns; R = 136 / 144 clusters 1043 / 1104 against 987 / 922)
+    bool grid = sms_dev > 0 && 8 * cluster_ctas <= 7 * sms_dev;
     if (!grid) {
       KernelFn cf = kernel_for(L, 4, 4, 512, bimodal);
       const size_t smem = (size_t)4 * 2 * words_per_cta(L, 4) * 4 + tab_bytes(4);

@@ -290,76 +290,132 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   if (!xa.enabled) return;
 
   // ---- energy partials (Eq. 1) per (replica, piece), then the exchange tail ----------------
-  // (the colour-1 halo planes hold the neighbours' final end planes, fetched by the last half-sweep)
-  __shared__ long long red_i[3][32];
-  __shared__ double red_d[32];
+  // (the colour-1 halo planes hold the neighbours' final end planes, fetched by the last half-sweep).
+  // As in the cluster plan's tail: up to RB replicas of a piece at a time (one field load per word
+  // for all of them, one barrier pair, then one warp per replica over the warps' partials); the
+  // float field term as exact fixed-point sums from the field limbs when given, else error-free
+  // float sums.
+  constexpr int RB = GG < kTailRB ? GG : kTailRB;
+  __shared__ int red_i[BIM ? 3 : 2][RB][32];
+  __shared__ long long red_l[BIM ? 1 : RB][32];
+  __shared__ double red_d[RB][32];
   __shared__ int last_cta;
   const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+  const bool limbs = !BIM && xa.flimb != nullptr;
   for (int p = 0; p < np; ++p) {
-    const int gact = pgact[p];
-    for (int gg = 0; gg < gact; ++gg) {
-      long long b = 0, m = 0, fi = 0;
-      float fs = 0.f, fe = 0.f;
-      for (int t = tid; t < pc[p].n * 2 * PW; t += nt) {
-        const int c = t / (pc[p].n * PW), rem = t % (pc[p].n * PW), pl = rem / PW, w = rem % PW;
+    const int gact = pgact[p], nwd = pc[p].n * PW;
+    for (int g0 = 0; g0 < gact; g0 += RB) {
+      const int ng = min(RB, gact - g0);
+      int b[RB], m[RB], fi[RB], hs[RB];
+      unsigned hu[RB][4];
+      float fs[RB], fe[RB];
+#pragma unroll
+      for (int gg = 0; gg < RB; ++gg) {
+        b[gg] = m[gg] = fi[gg] = hs[gg] = 0;
+        fs[gg] = fe[gg] = 0.f;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) hu[gg][l] = 0u;
+      }
+      for (int t = tid; t < 2 * nwd; t += nt) {
+        const int c = t / nwd, rem = t % nwd, pl = rem / PW, w = rem % PW;
         const int z = pc[p].z0 + pl;
         const int64_t wq = (int64_t)z * PW + w;
-        const uint32_t self = at(p, gg, c, pl)[w];
-        m += 2 * __popc(self) - 32;
-        if (c == 0) {
-          const uint32_t *O = at(p, gg, 1, pl);
-          uint32_t nbw[6];
-          nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], parity0_mask<L>(0, z, w), nbw[0], nbw[1], nbw[2], nbw[3]);
-          nbw[4] = O[PW + w];
-          nbw[5] = O[w - PW];
+        const uint32_t hb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+        uint32_t self[RB];
 #pragma unroll
-          for (int d = 0; d < 6; ++d) b += 32 - 2 * __popc(self ^ nbw[d]);
+        for (int gg = 0; gg < RB; ++gg) {
+          self[gg] = gg < ng ? at(p, g0 + gg, c, pl)[w] : 0u;
+          if (gg >= ng) continue;
+          m[gg] += 2 * __popc(self[gg]) - 32;
+          if (c == 0) {
+            const uint32_t *O = at(p, g0 + gg, 1, pl);
+            uint32_t nbw[6];
+            nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], parity0_mask<L>(0, z, w), nbw[0], nbw[1], nbw[2],
+                     nbw[3]);
+            nbw[4] = O[PW + w];
+            nbw[5] = O[w - PW];
+#pragma unroll
+            for (int d = 0; d < 6; ++d) b[gg] += 32 - 2 * __popc(self[gg] ^ nbw[d]);
+          }
+          if (BIM) fi[gg] += 32 - 2 * __popc(self[gg] ^ hb);
         }
-        if (BIM) {
-          fi += 32 - 2 * __popc(self ^ v.hbits[(int64_t)c * W + wq]);
-        } else {
+        if (limbs) {
+          const uint4 top0 = __ldg(xa.flimb + flimb_index(c, wq, 8, WPAD));
+          const uint4 top1 = __ldg(xa.flimb + flimb_index(c, wq, 9, WPAD));
+          const uint32_t top[8] = {top0.x, top0.y, top0.z, top0.w, top1.x, top1.y, top1.z, top1.w};
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint4 lo = __ldg(xa.flimb + flimb_index(c, wq, j, WPAD));
+#pragma unroll
+            for (int gg = 0; gg < RB; ++gg) {
+              if (gg >= ng) continue;
+              const uint32_t up = (self[gg] >> j) & 0x01010101u;
+              hu[gg][0] = __dp4a(up, lo.x, hu[gg][0]);
+              hu[gg][1] = __dp4a(up, lo.y, hu[gg][1]);
+              hu[gg][2] = __dp4a(up, lo.z, hu[gg][2]);
+              hu[gg][3] = __dp4a(up, lo.w, hu[gg][3]);
+              hs[gg] = __dp4a((int)up, (int)top[j], hs[gg]);
+            }
+          }
+        } else if (!BIM) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
             const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float term = ((self >> (8 * q + j)) & 1u) ? hk[q] : -hk[q];
-              const float tsum = __fadd_rn(fs, term);
-              const float bp = __fsub_rn(tsum, fs);
-              fe = __fadd_rn(fe, __fadd_rn(__fsub_rn(fs, __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
-              fs = tsum;
+            for (int gg = 0; gg < RB; ++gg) {
+              if (gg >= ng) continue;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float term = ((self[gg] >> (8 * q + j)) & 1u) ? hk[q] : -hk[q];
+                const float tsum = __fadd_rn(fs[gg], term);
+                const float bp = __fsub_rn(tsum, fs[gg]);
+                fe[gg] = __fadd_rn(fe[gg], __fadd_rn(__fsub_rn(fs[gg], __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
+                fs[gg] = tsum;
+              }
             }
           }
         }
       }
-      b = warp_reduce_sum(b);
-      m = warp_reduce_sum(m);
-      fi = warp_reduce_sum(fi);
-      double fd = warp_reduce_sum((double)fs + (double)fe);
-      if (lane == 0) {
-        red_i[0][wid] = b;
-        red_i[1][wid] = m;
-        red_i[2][wid] = fi;
-        red_d[wid] = fd;
+#pragma unroll
+      for (int gg = 0; gg < RB; ++gg) {
+        const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]);
+        if constexpr (BIM) {
+          const int tf = warp_reduce_sum(fi[gg]);
+          if (lane == 0) red_i[BIM ? 2 : 0][gg][wid] = tf;
+        } else {
+          long long fl = 0;
+          if (limbs)
+            fl = (long long)hu[gg][0] + ((long long)hu[gg][1] << 8) + ((long long)hu[gg][2] << 16) +
+                 ((long long)hu[gg][3] << 24) + ((long long)hs[gg] << 32);
+          const long long tf = warp_reduce_sum(fl);
+          if (lane == 0) red_l[BIM ? 0 : gg][wid] = tf;
+        }
+        const double td = (BIM || limbs) ? 0.0 : warp_reduce_sum((double)fs[gg] + (double)fe[gg]);
+        if (lane == 0) {
+          red_i[0][gg][wid] = tb;
+          red_i[1][gg][wid] = tm;
+          red_d[gg][wid] = td;
+        }
       }
       __syncthreads();
-      if (tid == 0) {
-        long long tb = 0, tm = 0, tf = 0;
-        double td = 0.0;
-        for (int w = 0; w < nw; ++w) {
-          tb += red_i[0][w];
-          tm += red_i[1][w];
-          tf += red_i[2][w];
-          td += red_d[w];
-        }
-        const int slab = grid_slab_of(ga.gp, k, pc[p].g);
-        const int64_t slot = (int64_t)(pc[p].g * GG + gg) * ga.slots + slab;
-        if (RFIM_DCHECK(xa.err, slab >= 0 && slab < ga.slots && pc[p].g * GG + gg < v.R, kDbgPartition)) {
-          ga.partB[slot] = tb;
-          ga.partM[slot] = tm;
-          ga.partFi[slot] = tf;
-          ga.partF[slot] = td;
+      if (wid < ng) {  // warp gg adds the warps' partials of replica g0 + gg of the piece
+        const int gg = wid;
+        const long long tb = warp_reduce_sum(lane < nw ? (long long)red_i[0][gg][lane] : 0LL);
+        const long long tm = warp_reduce_sum(lane < nw ? (long long)red_i[1][gg][lane] : 0LL);
+        const long long tf =
+            warp_reduce_sum(lane < nw ? (BIM ? (long long)red_i[BIM ? 2 : 0][gg][lane] : red_l[BIM ? 0 : gg][lane]) : 0LL);
+        const double td = warp_reduce_sum(lane < nw ? red_d[gg][lane] : 0.0);
+        if (lane == 0) {
+          const int slab = grid_slab_of(ga.gp, k, pc[p].g);
+          const int r = pc[p].g * GG + g0 + gg;
+          const int64_t slot = (int64_t)r * ga.slots + slab;
+          if (RFIM_DCHECK(xa.err, slab >= 0 && slab < ga.slots && r < v.R, kDbgPartition)) {
+            ga.partB[slot] = tb;
+            ga.partM[slot] = tm;
+            ga.partFi[slot] = tf;
+            ga.partF[slot] = td;
+          }
         }
       }
       __syncthreads();
@@ -384,7 +440,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
       tf += __ldcg(ga.partFi + slot);
       td += __ldcg(ga.partF + slot);
     }
-    const double F = BIM ? xa.h * (double)tf : td;
+    const double F = BIM ? xa.h * (double)tf
+                         : (xa.flimb ? ldexp((double)(2 * tf - xa.fquant->Htot), xa.fquant->qe) : td);
     v.E[r] = -xa.J * (double)tb - F;
     v.M[r] = tm;
   }

@@ -722,6 +722,18 @@ const char *rfim_last_error(const rfim_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 int64_t rfim_launch_count(const rfim_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+int rfim_get_plan(const rfim_ctx *ctx, char *plan_out, int32_t plan_cap) {
+  if (!ctx || !plan_out || plan_cap < 1) return RFIM_EINVAL;
+  const BitsPlan &p = ctx->plan;
+  if (!p.counter) {
+    plan_out[0] = '\0';
+    return RFIM_OK;
+  }
+  snprintf(plan_out, (size_t)plan_cap, "%d,%d,%d,%d%s%s", p.S, p.G, p.GT, p.threads, p.NS == 4 ? ",4" : "",
+           p.i8 ? ",int8" : "");
+  return RFIM_OK;
+}
+
 int rfim_tune(int32_t L, int32_t R, int32_t field_kind, char *plan_out, int32_t plan_cap, double *attempts_per_ns) {
   if (!bits_supported(L) || R < 2 || field_kind < 0 || field_kind > 2)
     return fail(nullptr, RFIM_EINVAL, "rfim_tune: L in {8,16,32,64}, R >= 2, known field kind");

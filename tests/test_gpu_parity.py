@@ -99,10 +99,15 @@ def test_bimodal_trajectory_bit_exact(L, R, layout, sweeps, ex):
     np.testing.assert_array_equal(E, np.array([o.energy(r)[0] for r in range(R)]))
 
 
-def test_bimodal_full_size_bit_exact():
-    """L = 64, R = 128 in the launch configuration the benchmark times, a few sweeps."""
+@pytest.mark.parametrize("plan", [None, "4,4,4,512"])
+def test_bimodal_full_size_bit_exact(plan, monkeypatch):
+    """L = 64, R = 128, a few sweeps: in the launch configuration the benchmark times (the default
+    plan, grid-wide at this R) and in clusters of four z slabs."""
+    if plan:
+        monkeypatch.setenv("RFIM_BITS_PLAN", plan)
     temps = inputs.geometric_temps(1.0, 5.0, 128)
     g, o = make_pair(64, temps, kind=BIM, layout=BP, h=1.0, field_seed=2, seed=42)
+    assert g.plan() == plan if plan else g.plan()
     g.run(4, 2, 0)
     o.run(4, 2, 0)
     assert_same_state(g, o, "full size")
