@@ -405,6 +405,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     if (!rc) rc = grab((void **)&p.prog, (size_t)std::max(sms, 1) * 4, "progress words");
   }
   if (!rc && cudaMemset(p.counter, 0, 8) != cudaSuccess) rc = -3;
+  if (!rc && p.prog && cudaMemset(p.prog, 0, (size_t)std::max(sms, 1) * 4) != cudaSuccess) rc = -3;
   if (rc) {
     free_bits_plan(p);
     return rc;
@@ -467,8 +468,14 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;
     GridArgs ga = grid_args(plan, v.R, plan.sms);
-    cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);
-    if (e != cudaSuccess) return e;
+    const uint32_t add = 2u * (uint32_t)n_sweeps;
+    if (plan.prog_base > 0xFFFFFFFFu - add) {  // the count would wrap: start again from zero
+      const cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);
+      if (e != cudaSuccess) return e;
+      plan.prog_base = 0;
+    }
+    ga.prog_base = plan.prog_base;
+    plan.prog_base += add;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ga.gp.P);
     cfg.blockDim = dim3((unsigned)plan.threads);
@@ -479,7 +486,9 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, gfn, v, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, gfn, v, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
+    if (le != cudaSuccess) plan.prog_base -= add;  // nothing ran: the words did not advance
+    return le;
   }
   const bool multihit = mh && mh->mh > 0;
   if (multihit && plan.S == 0) return cudaErrorInvalidConfiguration;

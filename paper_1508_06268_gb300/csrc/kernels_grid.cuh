@@ -25,7 +25,8 @@ constexpr unsigned kGridSpinLimit = 1u << 22;
 
 struct GridArgs {
   GridPart gp;
-  unsigned int *prog;  // [P] half-sweeps completed by each CTA in this launch (zeroed before it)
+  unsigned int *prog;  // [P] prog_base + half-sweeps completed by each CTA in this launch
+  uint32_t prog_base;  // every word's value when the launch starts
   int32_t max_units;   // units of the largest CTA (shared-memory sizing)
   int32_t slots;       // partial-sum slots per replica (CTAs sharing one group, at most)
   long long *partB, *partM, *partFi;  // [Rcap][slots]
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     }
   };
   // the neighbours' colour-1 end planes as the launch found them
-  fetch_halos(1, 0u, 0, nt, 1);
+  fetch_halos(1, ga.prog_base, 0, nt, 1);
   __syncthreads();
   GridHot hot;
   hot.lat = lat;
@@ -266,16 +267,16 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      st_release_u32(ga.prog + k, (unsigned)(h + 1));
+      st_release_u32(ga.prog + k, ga.prog_base + (unsigned)(h + 1));
     }
     // interior planes; warps without an item in the last round fetch the halos of the next
     // half-sweep (this colour's end planes of the neighbours), else every thread does afterwards
     process(split, items);
     if (idle_warps > 0) {
-      if (warp >= nt / 32 - idle_warps) fetch_halos(c, (unsigned)(h + 1), nt - 32 * idle_warps, 32 * idle_warps, 1);
+      if (warp >= nt / 32 - idle_warps) fetch_halos(c, ga.prog_base + (unsigned)(h + 1), nt - 32 * idle_warps, 32 * idle_warps, 1);
     } else {
       __syncthreads();
-      fetch_halos(c, (unsigned)(h + 1), 0, nt, 1);
+      fetch_halos(c, ga.prog_base + (unsigned)(h + 1), 0, nt, 1);
     }
     __syncthreads();
   }

@@ -205,6 +205,10 @@ int check_device_error(rfim_ctx *c) {
   CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
   if (!word) return RFIM_OK;
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.counter + 1, 0, 4, c->stream));
+  if (c->plan.prog) {  // an expired wait can leave the grid-wide kernel's progress words uneven
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.prog, 0, (size_t)std::max(c->plan.sms, 1) * 4, c->stream));
+    c->plan.prog_base = 0;
+  }
   if (word & kDbgMask)
     return fail(c, RFIM_EBOUNDS, "a bounds check of the debug build failed (error word 0x%x); the checked accesses were skipped", word);
   return fail(c, RFIM_ETIMEOUT, "a bounded device wait expired (error word %u); results of that launch are invalid", word);

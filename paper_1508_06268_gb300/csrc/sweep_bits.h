@@ -32,6 +32,9 @@ struct BitsPlan {
   long long *gpartB = nullptr, *gpartM = nullptr, *gpartFi = nullptr;
   double *gpartF = nullptr;
   unsigned int *prog = nullptr;
+  // progress count the grid-wide kernel's words held when the next launch starts (each launch
+  // adds its half-sweeps, so no launch has to zero them first)
+  mutable uint32_t prog_base = 0;
   int32_t sms = 0;
   bool i8 = false;  // the realization is stored in the int8 layout and staged as bits (cluster shapes)
   int32_t NS = 1;   // 4: every word split over four warps, one block pair each (small lattices)
