@@ -132,6 +132,10 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
   ga.max_units = maxu;
   ga.slots = slots;
   ga.prog = p.prog;
+  ga.prog_base = 0;
+  ga.n_iv = 1;
+  ga.x_base = 0;
+  ga.xdone = p.counter ? p.counter + 2 : nullptr;
   ga.partB = p.gpartB;
   ga.partM = p.gpartM;
   ga.partFi = p.gpartFi;
@@ -395,7 +399,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!rc) rc = grab((void **)&p.partM, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partFi, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partF, parts * 8, "partials");
-  if (!rc) rc = grab((void **)&p.counter, 8, "counter");
+  if (!rc) rc = grab((void **)&p.counter, 16, "counter");  // arrivals, error word, exchange steps done
   if (!rc && gfn) {
     const size_t gslots = (size_t)Rcap * (L + 1);
     rc = grab((void **)&p.gpartB, gslots * 8, "grid partials");
@@ -404,7 +408,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     if (!rc) rc = grab((void **)&p.gpartF, gslots * 8, "grid partials");
     if (!rc) rc = grab((void **)&p.prog, (size_t)std::max(sms, 1) * 4, "progress words");
   }
-  if (!rc && cudaMemset(p.counter, 0, 8) != cudaSuccess) rc = -3;
+  if (!rc && cudaMemset(p.counter, 0, 16) != cudaSuccess) rc = -3;
   if (!rc && p.prog && cudaMemset(p.prog, 0, (size_t)std::max(sms, 1) * 4) != cudaSuccess) rc = -3;
   if (rc) {
     free_bits_plan(p);
@@ -447,7 +451,7 @@ cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
 
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
                                bool exchange, uint32_t j, int64_t measure_from, double J, double h,
-                               cudaStream_t st, const MultiHit *mh) {
+                               cudaStream_t st, const MultiHit *mh, int32_t n_intervals) {
   ExchArgs xa{};
   xa.enabled = exchange ? 1 : 0;
   xa.j = j;
@@ -467,15 +471,25 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   if (plan.S == 0) {
     GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal);
     if (!gfn) return cudaErrorInvalidConfiguration;
+    if (n_intervals < 1) return cudaErrorInvalidValue;
     GridArgs ga = grid_args(plan, v.R, plan.sms);
-    const uint32_t add = 2u * (uint32_t)n_sweeps;
+    const uint32_t niv = (uint32_t)(exchange ? n_intervals : 1);
+    const uint32_t add = 2u * (uint32_t)n_sweeps * niv;
     if (plan.prog_base > 0xFFFFFFFFu - add) {  // the count would wrap: start again from zero
       const cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);
       if (e != cudaSuccess) return e;
       plan.prog_base = 0;
     }
+    if (plan.x_base > 0xFFFFFFFFu - niv) {
+      const cudaError_t e = cudaMemsetAsync(plan.counter + 2, 0, 4, st);
+      if (e != cudaSuccess) return e;
+      plan.x_base = 0;
+    }
     ga.prog_base = plan.prog_base;
+    ga.n_iv = (int32_t)niv;
+    ga.x_base = plan.x_base;
     plan.prog_base += add;
+    plan.x_base += niv;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ga.gp.P);
     cfg.blockDim = dim3((unsigned)plan.threads);
@@ -487,9 +501,13 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const cudaError_t le = cudaLaunchKernelEx(&cfg, gfn, v, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
-    if (le != cudaSuccess) plan.prog_base -= add;  // nothing ran: the words did not advance
+    if (le != cudaSuccess) {  // nothing ran: the words did not advance
+      plan.prog_base -= add;
+      plan.x_base -= niv;
+    }
     return le;
   }
+  if (n_intervals != 1) return cudaErrorInvalidValue;  // several intervals: grid-wide plan only
   const bool multihit = mh && mh->mh > 0;
   if (multihit && plan.S == 0) return cudaErrorInvalidConfiguration;
   KernelFn fn = multihit ? nullptr : kernel_for(plan.L, plan.S, plan.GT, plan.threads, v.kind == kBimodal, plan.i8, plan.NS);

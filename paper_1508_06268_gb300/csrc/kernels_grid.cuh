@@ -27,6 +27,11 @@ struct GridArgs {
   GridPart gp;
   unsigned int *prog;  // [P] prog_base + half-sweeps completed by each CTA in this launch
   uint32_t prog_base;  // every word's value when the launch starts
+  // exchange intervals in this launch (with the fused exchange); between them the other CTAs wait
+  // for the last one's release of *xdone = x_base + interval + 1
+  int32_t n_iv;
+  uint32_t x_base;
+  unsigned int *xdone;
   int32_t max_units;   // units of the largest CTA (shared-memory sizing)
   int32_t slots;       // partial-sum slots per replica (CTAs sharing one group, at most)
   long long *partB, *partM, *partFi;  // [Rcap][slots]
@@ -253,202 +258,228 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   hot.pcs = pcs;
   hot.pgact = pgact;
 
-  for (int h = 0; h < 2 * nsw; ++h) {
-    const int c = h & 1, other = c ^ 1;
-    const uint32_t sweep = sweep0 + (uint32_t)(h >> 1);
-    const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)c);
-    auto process = [&](int i0, int i1) {
-      grid_process<L, BIM, GG, GTI>(hot, i0, i1, c, sweep, tag);
-    };
-    // end planes (and the interior items sharing their rounds), then the progress word: the CTA
-    // barrier orders every thread's end-plane stores before thread 0's gpu-scope fence and release
-    // (cumulativity), as in a grid-wide barrier
-    process(0, split);
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release_u32(ga.prog + k, ga.prog_base + (unsigned)(h + 1));
-    }
-    // interior planes; warps without an item in the last round fetch the halos of the next
-    // half-sweep (this colour's end planes of the neighbours), else every thread does afterwards
-    process(split, items);
-    if (idle_warps > 0) {
-      if (warp >= nt / 32 - idle_warps) fetch_halos(c, ga.prog_base + (unsigned)(h + 1), nt - 32 * idle_warps, 32 * idle_warps, 1);
-    } else {
+  // Several exchange intervals per launch (fused exchange, ga.n_iv > 1): after each interval's
+  // exchange step, taken by the last CTA to arrive, the other CTAs wait for its release of xdone
+  // and refill their decision tables for the new temperature assignment.
+  const int n_iv = xa.enabled ? max(ga.n_iv, 1) : 1;
+  for (int iv = 0; iv < n_iv; ++iv) {
+    const unsigned pbase = ga.prog_base + (unsigned)(2 * nsw * iv);
+    if (iv > 0) {
+      tab_fill<BIM, true>(v, tab, slot0, np * GG, [&](int t) { return min(pc[t / GG].g * GG + t % GG, v.R - 1); });
       __syncthreads();
-      fetch_halos(c, ga.prog_base + (unsigned)(h + 1), 0, nt, 1);
     }
-    __syncthreads();
-  }
-
-  for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
-    const int lu = t / (GG * 2 * PW), rem = t % (GG * 2 * PW), gg = rem / (2 * PW), c = (rem / PW) & 1, w = rem % PW;
-    const uint32_t d = udesc[lu];
-    const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
-    const int r = pc[p].g * GG + gg, z = pc[p].z0 + zl;
-    if (r < v.R) v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = at(p, gg, c, zl)[w];
-  }
-  if (!xa.enabled) return;
-
-  // ---- energy partials (Eq. 1) per (replica, piece), then the exchange tail ----------------
-  // (the colour-1 halo planes hold the neighbours' final end planes, fetched by the last half-sweep).
-  // As in the cluster plan's tail: up to RB replicas of a piece at a time (one field load per word
-  // for all of them, one barrier pair, then one warp per replica over the warps' partials); the
-  // float field term as exact fixed-point sums from the field limbs when given, else error-free
-  // float sums.
-  constexpr int RB = GG < kTailRB ? GG : kTailRB;
-  __shared__ int red_i[BIM ? 3 : 2][RB][32];
-  __shared__ long long red_l[BIM ? 1 : RB][32];
-  __shared__ double red_d[RB][32];
-  __shared__ int last_cta;
-  const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
-  const bool limbs = !BIM && xa.flimb != nullptr;
-  for (int p = 0; p < np; ++p) {
-    const int gact = pgact[p], nwd = pc[p].n * PW;
-    for (int g0 = 0; g0 < gact; g0 += RB) {
-      const int ng = min(RB, gact - g0);
-      int b[RB], m[RB], fi[RB], hs[RB];
-      unsigned hu[RB][4];
-      float fs[RB], fe[RB];
-#pragma unroll
-      for (int gg = 0; gg < RB; ++gg) {
-        b[gg] = m[gg] = fi[gg] = hs[gg] = 0;
-        fs[gg] = fe[gg] = 0.f;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) hu[gg][l] = 0u;
+    for (int h = 0; h < 2 * nsw; ++h) {
+      const int c = h & 1, other = c ^ 1;
+      const uint32_t sweep = sweep0 + (uint32_t)(iv * nsw + (h >> 1));
+      const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)c);
+      auto process = [&](int i0, int i1) {
+        grid_process<L, BIM, GG, GTI>(hot, i0, i1, c, sweep, tag);
+      };
+      // end planes (and the interior items sharing their rounds), then the progress word: the CTA
+      // barrier orders every thread's end-plane stores before thread 0's gpu-scope fence and release
+      // (cumulativity), as in a grid-wide barrier
+      process(0, split);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release_u32(ga.prog + k, pbase + (unsigned)(h + 1));
       }
-      for (int t = tid; t < 2 * nwd; t += nt) {
-        const int c = t / nwd, rem = t % nwd, pl = rem / PW, w = rem % PW;
-        const int z = pc[p].z0 + pl;
-        const int64_t wq = (int64_t)z * PW + w;
-        const uint32_t hb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
-        uint32_t self[RB];
-#pragma unroll
+      // interior planes; warps without an item in the last round fetch the halos of the next
+      // half-sweep (this colour's end planes of the neighbours), else every thread does afterwards
+      process(split, items);
+      if (idle_warps > 0) {
+        if (warp >= nt / 32 - idle_warps) fetch_halos(c, pbase + (unsigned)(h + 1), nt - 32 * idle_warps, 32 * idle_warps, 1);
+      } else {
+        __syncthreads();
+        fetch_halos(c, pbase + (unsigned)(h + 1), 0, nt, 1);
+      }
+      __syncthreads();
+    }
+
+    if (iv == n_iv - 1) {  // the lattice back to global memory once, after the last interval
+      for (int t = tid; t < nu * GG * 2 * PW; t += nt) {
+        const int lu = t / (GG * 2 * PW), rem = t % (GG * 2 * PW), gg = rem / (2 * PW), c = (rem / PW) & 1, w = rem % PW;
+        const uint32_t d = udesc[lu];
+        const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
+        const int r = pc[p].g * GG + gg, z = pc[p].z0 + zl;
+        if (r < v.R) v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = at(p, gg, c, zl)[w];
+      }
+    }
+    if (!xa.enabled) return;
+
+    // ---- energy partials (Eq. 1) per (replica, piece), then the exchange tail ----------------
+    // (the colour-1 halo planes hold the neighbours' final end planes, fetched by the last half-sweep).
+    // As in the cluster plan's tail: up to RB replicas of a piece at a time (one field load per word
+    // for all of them, one barrier pair, then one warp per replica over the warps' partials); the
+    // float field term as exact fixed-point sums from the field limbs when given, else error-free
+    // float sums.
+    constexpr int RB = GG < kTailRB ? GG : kTailRB;
+    __shared__ int red_i[BIM ? 3 : 2][RB][32];
+    __shared__ long long red_l[BIM ? 1 : RB][32];
+    __shared__ double red_d[RB][32];
+    __shared__ int last_cta;
+    const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+    const bool limbs = !BIM && xa.flimb != nullptr;
+    for (int p = 0; p < np; ++p) {
+      const int gact = pgact[p], nwd = pc[p].n * PW;
+      for (int g0 = 0; g0 < gact; g0 += RB) {
+        const int ng = min(RB, gact - g0);
+        int b[RB], m[RB], fi[RB], hs[RB];
+        unsigned hu[RB][4];
+        float fs[RB], fe[RB];
+  #pragma unroll
         for (int gg = 0; gg < RB; ++gg) {
-          self[gg] = gg < ng ? at(p, g0 + gg, c, pl)[w] : 0u;
-          if (gg >= ng) continue;
-          m[gg] += 2 * __popc(self[gg]) - 32;
-          if (c == 0) {
-            const uint32_t *O = at(p, g0 + gg, 1, pl);
-            uint32_t nbw[6];
-            nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], parity0_mask<L>(0, z, w), nbw[0], nbw[1], nbw[2],
-                     nbw[3]);
-            nbw[4] = O[PW + w];
-            nbw[5] = O[w - PW];
-#pragma unroll
-            for (int d = 0; d < 6; ++d) b[gg] += 32 - 2 * __popc(self[gg] ^ nbw[d]);
-          }
-          if (BIM) fi[gg] += 32 - 2 * __popc(self[gg] ^ hb);
+          b[gg] = m[gg] = fi[gg] = hs[gg] = 0;
+          fs[gg] = fe[gg] = 0.f;
+  #pragma unroll
+          for (int l = 0; l < 4; ++l) hu[gg][l] = 0u;
         }
-        if (limbs) {
-          const uint4 top0 = __ldg(xa.flimb + flimb_index(c, wq, 8, WPAD));
-          const uint4 top1 = __ldg(xa.flimb + flimb_index(c, wq, 9, WPAD));
-          const uint32_t top[8] = {top0.x, top0.y, top0.z, top0.w, top1.x, top1.y, top1.z, top1.w};
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const uint4 lo = __ldg(xa.flimb + flimb_index(c, wq, j, WPAD));
-#pragma unroll
-            for (int gg = 0; gg < RB; ++gg) {
-              if (gg >= ng) continue;
-              const uint32_t up = (self[gg] >> j) & 0x01010101u;
-              hu[gg][0] = __dp4a(up, lo.x, hu[gg][0]);
-              hu[gg][1] = __dp4a(up, lo.y, hu[gg][1]);
-              hu[gg][2] = __dp4a(up, lo.z, hu[gg][2]);
-              hu[gg][3] = __dp4a(up, lo.w, hu[gg][3]);
-              hs[gg] = __dp4a((int)up, (int)top[j], hs[gg]);
+        for (int t = tid; t < 2 * nwd; t += nt) {
+          const int c = t / nwd, rem = t % nwd, pl = rem / PW, w = rem % PW;
+          const int z = pc[p].z0 + pl;
+          const int64_t wq = (int64_t)z * PW + w;
+          const uint32_t hb = BIM ? v.hbits[(int64_t)c * W + wq] : 0u;
+          uint32_t self[RB];
+  #pragma unroll
+          for (int gg = 0; gg < RB; ++gg) {
+            self[gg] = gg < ng ? at(p, g0 + gg, c, pl)[w] : 0u;
+            if (gg >= ng) continue;
+            m[gg] += 2 * __popc(self[gg]) - 32;
+            if (c == 0) {
+              const uint32_t *O = at(p, g0 + gg, 1, pl);
+              uint32_t nbw[6];
+              nb_xy<L>(O[w], O[(w + 1) % PW], O[(w + PW - 1) % PW], parity0_mask<L>(0, z, w), nbw[0], nbw[1], nbw[2],
+                       nbw[3]);
+              nbw[4] = O[PW + w];
+              nbw[5] = O[w - PW];
+  #pragma unroll
+              for (int d = 0; d < 6; ++d) b[gg] += 32 - 2 * __popc(self[gg] ^ nbw[d]);
             }
+            if (BIM) fi[gg] += 32 - 2 * __popc(self[gg] ^ hb);
           }
-        } else if (!BIM) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
-            const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-            for (int gg = 0; gg < RB; ++gg) {
-              if (gg >= ng) continue;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float term = ((self[gg] >> (8 * q + j)) & 1u) ? hk[q] : -hk[q];
-                const float tsum = __fadd_rn(fs[gg], term);
-                const float bp = __fsub_rn(tsum, fs[gg]);
-                fe[gg] = __fadd_rn(fe[gg], __fadd_rn(__fsub_rn(fs[gg], __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
-                fs[gg] = tsum;
+          if (limbs) {
+            const uint4 top0 = __ldg(xa.flimb + flimb_index(c, wq, 8, WPAD));
+            const uint4 top1 = __ldg(xa.flimb + flimb_index(c, wq, 9, WPAD));
+            const uint32_t top[8] = {top0.x, top0.y, top0.z, top0.w, top1.x, top1.y, top1.z, top1.w};
+  #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const uint4 lo = __ldg(xa.flimb + flimb_index(c, wq, j, WPAD));
+  #pragma unroll
+              for (int gg = 0; gg < RB; ++gg) {
+                if (gg >= ng) continue;
+                const uint32_t up = (self[gg] >> j) & 0x01010101u;
+                hu[gg][0] = __dp4a(up, lo.x, hu[gg][0]);
+                hu[gg][1] = __dp4a(up, lo.y, hu[gg][1]);
+                hu[gg][2] = __dp4a(up, lo.z, hu[gg][2]);
+                hu[gg][3] = __dp4a(up, lo.w, hu[gg][3]);
+                hs[gg] = __dp4a((int)up, (int)top[j], hs[gg]);
+              }
+            }
+          } else if (!BIM) {
+  #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 q4 = __ldg(field4 + field4_index(c, wq, j, WPAD));
+              const float hk[4] = {q4.x, q4.y, q4.z, q4.w};
+  #pragma unroll
+              for (int gg = 0; gg < RB; ++gg) {
+                if (gg >= ng) continue;
+  #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const float term = ((self[gg] >> (8 * q + j)) & 1u) ? hk[q] : -hk[q];
+                  const float tsum = __fadd_rn(fs[gg], term);
+                  const float bp = __fsub_rn(tsum, fs[gg]);
+                  fe[gg] = __fadd_rn(fe[gg], __fadd_rn(__fsub_rn(fs[gg], __fsub_rn(tsum, bp)), __fsub_rn(term, bp)));
+                  fs[gg] = tsum;
+                }
               }
             }
           }
         }
-      }
-#pragma unroll
-      for (int gg = 0; gg < RB; ++gg) {
-        const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]);
-        if constexpr (BIM) {
-          const int tf = warp_reduce_sum(fi[gg]);
-          if (lane == 0) red_i[BIM ? 2 : 0][gg][wid] = tf;
-        } else {
-          long long fl = 0;
-          if (limbs)
-            fl = (long long)hu[gg][0] + ((long long)hu[gg][1] << 8) + ((long long)hu[gg][2] << 16) +
-                 ((long long)hu[gg][3] << 24) + ((long long)hs[gg] << 32);
-          const long long tf = warp_reduce_sum(fl);
-          if (lane == 0) red_l[BIM ? 0 : gg][wid] = tf;
-        }
-        const double td = (BIM || limbs) ? 0.0 : warp_reduce_sum((double)fs[gg] + (double)fe[gg]);
-        if (lane == 0) {
-          red_i[0][gg][wid] = tb;
-          red_i[1][gg][wid] = tm;
-          red_d[gg][wid] = td;
-        }
-      }
-      __syncthreads();
-      if (wid < ng) {  // warp gg adds the warps' partials of replica g0 + gg of the piece
-        const int gg = wid;
-        const long long tb = warp_reduce_sum(lane < nw ? (long long)red_i[0][gg][lane] : 0LL);
-        const long long tm = warp_reduce_sum(lane < nw ? (long long)red_i[1][gg][lane] : 0LL);
-        const long long tf =
-            warp_reduce_sum(lane < nw ? (BIM ? (long long)red_i[BIM ? 2 : 0][gg][lane] : red_l[BIM ? 0 : gg][lane]) : 0LL);
-        const double td = warp_reduce_sum(lane < nw ? red_d[gg][lane] : 0.0);
-        if (lane == 0) {
-          const int slab = grid_slab_of(ga.gp, k, pc[p].g);
-          const int r = pc[p].g * GG + g0 + gg;
-          const int64_t slot = (int64_t)r * ga.slots + slab;
-          if (RFIM_DCHECK(xa.err, slab >= 0 && slab < ga.slots && r < v.R, kDbgPartition)) {
-            ga.partB[slot] = tb;
-            ga.partM[slot] = tm;
-            ga.partFi[slot] = tf;
-            ga.partF[slot] = td;
+  #pragma unroll
+        for (int gg = 0; gg < RB; ++gg) {
+          const int tb = warp_reduce_sum(b[gg]), tm = warp_reduce_sum(m[gg]);
+          if constexpr (BIM) {
+            const int tf = warp_reduce_sum(fi[gg]);
+            if (lane == 0) red_i[BIM ? 2 : 0][gg][wid] = tf;
+          } else {
+            long long fl = 0;
+            if (limbs)
+              fl = (long long)hu[gg][0] + ((long long)hu[gg][1] << 8) + ((long long)hu[gg][2] << 16) +
+                   ((long long)hu[gg][3] << 24) + ((long long)hs[gg] << 32);
+            const long long tf = warp_reduce_sum(fl);
+            if (lane == 0) red_l[BIM ? 0 : gg][wid] = tf;
+          }
+          const double td = (BIM || limbs) ? 0.0 : warp_reduce_sum((double)fs[gg] + (double)fe[gg]);
+          if (lane == 0) {
+            red_i[0][gg][wid] = tb;
+            red_i[1][gg][wid] = tm;
+            red_d[gg][wid] = td;
           }
         }
+        __syncthreads();
+        if (wid < ng) {  // warp gg adds the warps' partials of replica g0 + gg of the piece
+          const int gg = wid;
+          const long long tb = warp_reduce_sum(lane < nw ? (long long)red_i[0][gg][lane] : 0LL);
+          const long long tm = warp_reduce_sum(lane < nw ? (long long)red_i[1][gg][lane] : 0LL);
+          const long long tf =
+              warp_reduce_sum(lane < nw ? (BIM ? (long long)red_i[BIM ? 2 : 0][gg][lane] : red_l[BIM ? 0 : gg][lane]) : 0LL);
+          const double td = warp_reduce_sum(lane < nw ? red_d[gg][lane] : 0.0);
+          if (lane == 0) {
+            const int slab = grid_slab_of(ga.gp, k, pc[p].g);
+            const int r = pc[p].g * GG + g0 + gg;
+            const int64_t slot = (int64_t)r * ga.slots + slab;
+            if (RFIM_DCHECK(xa.err, slab >= 0 && slab < ga.slots && r < v.R, kDbgPartition)) {
+              ga.partB[slot] = tb;
+              ga.partM[slot] = tm;
+              ga.partFi[slot] = tf;
+              ga.partF[slot] = td;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (tid == 0) {
+      __threadfence();
+      last_cta = atomicAdd(xa.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last_cta) {
+      __threadfence();
+      for (int r = tid; r < v.R; r += nt) {
+        const int g = r / GG;
+        const int nslab = grid_owner(ga.gp, (int64_t)g * L + L - 1) - grid_owner(ga.gp, (int64_t)g * L) + 1;
+        long long tb = 0, tm = 0, tf = 0;
+        double td = 0.0;
+        for (int q = 0; q < nslab; ++q) {
+          const int64_t slot = (int64_t)r * ga.slots + q;
+          tb += __ldcg(ga.partB + slot);
+          tm += __ldcg(ga.partM + slot);
+          tf += __ldcg(ga.partFi + slot);
+          td += __ldcg(ga.partF + slot);
+        }
+        const double F = BIM ? xa.h * (double)tf
+                             : (xa.flimb ? ldexp((double)(2 * tf - xa.fquant->Htot), xa.fquant->qe) : td);
+        v.E[r] = -xa.J * (double)tb - F;
+        v.M[r] = tm;
       }
       __syncthreads();
+      if (n_iv > 1)
+        exchange_and_measure<true>(v, xa.j + (uint32_t)iv, xa.measure_from);
+      else
+        exchange_and_measure(v, xa.j, xa.measure_from);
+      if (tid == 0) {
+        *xa.counter = 0u;
+        if (iv + 1 < n_iv) {
+          __threadfence();
+          st_release_u32(ga.xdone, ga.x_base + (unsigned)(iv + 1));
+        }
+      }
+    } else if (iv + 1 < n_iv && tid == 0) {
+      grid_wait(ga.xdone, 0, ga.x_base + (unsigned)(iv + 1), err);
     }
-  }
-  if (tid == 0) {
-    __threadfence();
-    last_cta = atomicAdd(xa.counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last_cta) return;
-  __threadfence();
-  for (int r = tid; r < v.R; r += nt) {
-    const int g = r / GG;
-    const int nslab = grid_owner(ga.gp, (int64_t)g * L + L - 1) - grid_owner(ga.gp, (int64_t)g * L) + 1;
-    long long tb = 0, tm = 0, tf = 0;
-    double td = 0.0;
-    for (int q = 0; q < nslab; ++q) {
-      const int64_t slot = (int64_t)r * ga.slots + q;
-      tb += __ldcg(ga.partB + slot);
-      tm += __ldcg(ga.partM + slot);
-      tf += __ldcg(ga.partFi + slot);
-      td += __ldcg(ga.partF + slot);
-    }
-    const double F = BIM ? xa.h * (double)tf
-                         : (xa.flimb ? ldexp((double)(2 * tf - xa.fquant->Htot), xa.fquant->qe) : td);
-    v.E[r] = -xa.J * (double)tb - F;
-    v.M[r] = tm;
-  }
-  __syncthreads();
-  exchange_and_measure(v, xa.j, xa.measure_from);
-  if (tid == 0) *xa.counter = 0u;
+    __syncthreads();
+  }  // exchange intervals
 }
 
 }  // namespace rfim

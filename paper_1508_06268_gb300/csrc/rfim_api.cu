@@ -54,6 +54,7 @@ struct rfim_ctx {
   // optional kernel timing: event pairs around sweep launches (kind 0) and energy+exchange (kind 1)
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used[2], ev_free;
+  int64_t prof_units[2] = {0, 0};  // bracketed groups (a launch of K exchange intervals counts K)
 };
 
 namespace {
@@ -112,9 +113,10 @@ RealView view_of(const rfim_ctx *c) {
   return v;
 }
 
-cudaError_t prof_begin(rfim_ctx *c, int kind, cudaEvent_t *stop_out) {
+cudaError_t prof_begin(rfim_ctx *c, int kind, cudaEvent_t *stop_out, int64_t units = 1) {
   *stop_out = nullptr;
   if (!c->profiling) return cudaSuccess;
+  c->prof_units[kind] += units;
   std::pair<cudaEvent_t, cudaEvent_t> ev;
   if (!c->ev_free.empty()) {
     ev = c->ev_free.back();
@@ -207,7 +209,9 @@ int check_device_error(rfim_ctx *c) {
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.counter + 1, 0, 4, c->stream));
   if (c->plan.prog) {  // an expired wait can leave the grid-wide kernel's progress words uneven
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.prog, 0, (size_t)std::max(c->plan.sms, 1) * 4, c->stream));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.counter + 2, 0, 4, c->stream));
     c->plan.prog_base = 0;
+    c->plan.x_base = 0;
   }
   if (word & kDbgMask)
     return fail(c, RFIM_EBOUNDS, "a bounds check of the debug build failed (error word 0x%x); the checked accesses were skipped", word);
@@ -245,19 +249,23 @@ int measure_xi_after(rfim_ctx *c, int64_t j, int64_t measure_from) {
   return RFIM_OK;
 }
 
-// Bit layout: n sweeps and the exchange step in one launch (fused tail).
-int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from) {
+// Bit layout: n sweeps and the exchange step in one launch (fused tail); with the grid-wide plan,
+// k such intervals in one launch.
+int do_sweeps_exchange_bits(rfim_ctx *c, int64_t n, int64_t measure_from, int32_t k = 1) {
   RealView v = view_of(c);
   cudaEvent_t stop;
-  CUDA_OR_FAIL(c, prof_begin(c, 0, &stop));
+  CUDA_OR_FAIL(c, prof_begin(c, 0, &stop, k));
   CUDA_OR_FAIL(c, launch_sweeps_bits(v, c->plan, (uint32_t)c->sweep, (int32_t)n, true, (uint32_t)c->xstep,
-                                     measure_from, (double)c->J, (double)c->h, c->stream, &c->mh));
+                                     measure_from, (double)c->J, (double)c->h, c->stream, &c->mh, k));
   CUDA_OR_FAIL(c, prof_end(c, stop));
   c->launches += 1;
-  c->sweep += n;
-  c->xstep += 1;
+  c->sweep += n * k;
+  c->xstep += k;
   return measure_xi_after(c, c->xstep - 1, measure_from);
 }
+
+// Exchange intervals one grid-wide launch takes at most (the host regains control between them).
+constexpr int64_t kMaxIntervalsPerLaunch = 64;
 
 int do_exchange(rfim_ctx *c, int64_t measure_from) {
   if (c->plan.counter) return do_sweeps_exchange_bits(c, 0, measure_from);
@@ -283,6 +291,16 @@ int do_run(rfim_ctx *c, int64_t n_sweeps, int32_t ex, int64_t measure_from) {
     }
     const bool ends_interval = ex > 0 && (c->sweep + chunk) % ex == 0;
     int rc;
+    // whole intervals on the grid-wide plan: several per launch (not with the structure factor,
+    // which a separate kernel measures after every exchange step, nor with multi-hit)
+    if (ends_interval && chunk == ex && left >= 2 * (int64_t)ex && c->plan.counter && c->plan.S == 0 &&
+        !c->xi_on && c->mh.mh == 0) {
+      const int64_t k = std::min(left / ex, kMaxIntervalsPerLaunch);
+      rc = do_sweeps_exchange_bits(c, ex, measure_from, (int32_t)k);
+      if (rc) return rc;
+      left -= k * ex;
+      continue;
+    }
     if (ends_interval && c->plan.counter) {
       rc = do_sweeps_exchange_bits(c, chunk, measure_from);
       if (rc) return rc;
@@ -798,6 +816,7 @@ int rfim_profile(rfim_ctx *ctx, int enable) {
     for (auto &p : v) ctx->ev_free.push_back(p);
     v.clear();
   }
+  ctx->prof_units[0] = ctx->prof_units[1] = 0;
   ctx->profiling = enable != 0;
   return RFIM_OK;
 }
@@ -814,9 +833,9 @@ int rfim_profile_read(rfim_ctx *ctx, double *sweep_ms, int64_t *sweep_launches, 
       tot[k] += ms;
     }
   if (sweep_ms) *sweep_ms = tot[0];
-  if (sweep_launches) *sweep_launches = (int64_t)ctx->ev_used[0].size();
+  if (sweep_launches) *sweep_launches = ctx->prof_units[0];
   if (exchange_ms) *exchange_ms = tot[1];
-  if (exchange_launches) *exchange_launches = (int64_t)ctx->ev_used[1].size();
+  if (exchange_launches) *exchange_launches = ctx->prof_units[1];
   return RFIM_OK;
 }
 

@@ -35,6 +35,7 @@ struct BitsPlan {
   // progress count the grid-wide kernel's words held when the next launch starts (each launch
   // adds its half-sweeps, so no launch has to zero them first)
   mutable uint32_t prog_base = 0;
+  mutable uint32_t x_base = 0;  // the same for the exchange-step word (counter[2])
   int32_t sms = 0;
   bool i8 = false;  // the realization is stored in the int8 layout and staged as bits (cluster shapes)
   int32_t NS = 1;   // 4: every word split over four warps, one block pair each (small lattices)
@@ -69,8 +70,10 @@ void free_bits_plan(BitsPlan &plan);
 // n_sweeps sweeps; when exchange is true the launch ends with exchange step j (energies, swap
 // decisions, permutation, measurement when j >= measure_from).
 // With mh set (mh->mh > 0) the sweeps are multi-hit double-checkerboard sweeps.
+// n_intervals > 1 (grid-wide plan with the exchange only): that many exchange intervals of n_sweeps
+// sweeps each in one launch, exchange steps j, j + 1, ...
 cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t sweep0, int32_t n_sweeps,
                                bool exchange, uint32_t j, int64_t measure_from, double J, double h,
-                               cudaStream_t st, const MultiHit *mh = nullptr);
+                               cudaStream_t st, const MultiHit *mh = nullptr, int32_t n_intervals = 1);
 
 }  // namespace rfim

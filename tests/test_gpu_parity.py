@@ -429,15 +429,48 @@ def test_grid_wide_variant_bit_exact(L, R, plan, monkeypatch):
     np.testing.assert_array_equal(g.observables()["sums"], o.observables())
 
 
+@pytest.mark.parametrize("kind", [BIM, EXP])
+def test_grid_wide_many_intervals_per_launch(kind, monkeypatch):
+    """The grid-wide plan runs up to 64 exchange intervals per launch (the last CTA's exchange step
+    released to the others in between); 100 intervals (launches of 64 and 36) give the spins,
+    permutation, exchange counts and measurement sums of the cluster plan, which launches once per
+    interval: bit for bit with the bimodal field, to rounding of the sums with a float field."""
+    L, R = 64, 8
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    field = inputs.gaussian_field(L, 9) if kind == EXP else None
+    runs = []
+    for plan in ("4,4,4,512", "0,4,4,512"):
+        monkeypatch.setenv("RFIM_BITS_PLAN", plan)
+        g = rf.Realization(L, temps, h=1.5, field_kind=kind, field=field, field_seed=4, seed=11, layout=BP)
+        assert g.plan() == plan
+        n0 = g.launch_count
+        g.run(200, 2, 60)
+        runs.append((g.get_state(), g.observables(), g.launch_count - n0))
+        g.close()
+    monkeypatch.delenv("RFIM_BITS_PLAN")
+    (sa, oa, na), (sb, ob, nb) = runs
+    assert na - nb == 98  # 100 interval launches against 2 (any set-up launch counts in both)
+    assert sa["xstep"] == sb["xstep"] == 100 and sa["sweep"] == sb["sweep"] == 200
+    np.testing.assert_array_equal(sa["spins"], sb["spins"])
+    np.testing.assert_array_equal(sa["t2r"], sb["t2r"])
+    np.testing.assert_array_equal(oa["acc"], ob["acc"])
+    assert oa["n_meas"] == ob["n_meas"] == 40
+    if kind == BIM:
+        np.testing.assert_array_equal(oa["sums"], ob["sums"])
+    else:
+        np.testing.assert_allclose(oa["sums"], ob["sums"], rtol=1e-12)
+
+
 @pytest.mark.parametrize("plan", ["0,4,4,512", "0,4,1,512", "0,4,2,896", "0,8,8,512"])
 def test_grid_wide_variant_gaussian_matches_cluster_plan(plan, monkeypatch):
-    """Gaussian field: the grid-wide plans take the same decisions as the default cluster plan
-    (spins and permutation identical; energies summed over other slab boundaries agree to
-    rounding)."""
+    """Gaussian field: the grid-wide plans take the same decisions as the cluster plan (spins and
+    permutation identical; energies summed over other slab boundaries agree to rounding)."""
     L, R = 64, 10
     temps = inputs.geometric_temps(1.0, 5.0, R)
     field = inputs.gaussian_field(L, 77)
+    monkeypatch.setenv("RFIM_BITS_PLAN", "4,4,4,512")
     ref = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP, seed=5)
+    assert ref.plan() == "4,4,4,512"
     monkeypatch.setenv("RFIM_BITS_PLAN", plan)
     grid = rf.Realization(L, temps, field_kind=EXP, field=field, layout=BP, seed=5)
     monkeypatch.delenv("RFIM_BITS_PLAN")
