@@ -43,7 +43,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
 # (one exchange interval, 3.36e8 attempts, in either layout) from
 # one ncu capture of the current kernel version; None when the kernel changed since the capture.
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.711296e6,
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.724096e6,
                        "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6}
 
 
@@ -350,7 +350,8 @@ def run_profile(args):
         layout = rf.LAYOUT_INT8 if case == "c4-int8" else rf.LAYOUT_BITPACK
         kind = rf.FIELD_BIMODAL if case == "c4-bimodal" else rf.FIELD_GAUSSIAN
         g = rf.Realization(L, inputs.geometric_temps(T_MIN, T_MAX, R), field_kind=kind, layout=layout)
-        g.run(40, EX, 0)
+        for _ in range(4):  # one exchange interval per call, so one per launch in every plan
+            g.run(EX, EX, 0)
         print("ok", g.get_state(spins=False)["sweep"])
     torch.cuda.synchronize()
 

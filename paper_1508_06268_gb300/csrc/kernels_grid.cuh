@@ -77,7 +77,8 @@ struct GridHot {
 };
 
 template <int L, bool BIM, int GG, int GTI>
-__device__ __noinline__ void grid_process(const GridHot hot, int i0, int i1, int c, uint32_t sweep, uint32_t tag) {
+__device__ __noinline__ void grid_process(const GridHot *hot_s, int i0, int i1, int c, uint32_t sweep, uint32_t tag) {
+  const GridHot hot = *hot_s;  // from shared memory: the caller keeps none of it in registers
   constexpr int PW = L * L / 64, W = L * L * L / 64;
   constexpr int64_t WPAD = (W + 31) / 32 * 32;
   constexpr int IPW = PW * (GG / GTI);
@@ -240,23 +241,25 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   };
   // the neighbours' colour-1 end planes as the launch found them
   fetch_halos(1, ga.prog_base, 0, nt, 1);
+  __shared__ GridHot hot;
+  if (tid == 0) {
+    hot.lat = lat;
+    hot.field4 = field4;
+    hot.bits = v.bits;
+    hot.hbits = v.hbits;
+    hot.seed = v.seed;
+    hot.realization = v.realization;
+    hot.slot0 = slot0;
+    hot.nb_items = nb * IPW;
+    hot.np = np;
+    hot.err = err;
+    hot.desc = udesc;
+    hot.order = order;
+    hot.pc = pc;
+    hot.pcs = pcs;
+    hot.pgact = pgact;
+  }
   __syncthreads();
-  GridHot hot;
-  hot.lat = lat;
-  hot.field4 = field4;
-  hot.bits = v.bits;
-  hot.hbits = v.hbits;
-  hot.seed = v.seed;
-  hot.realization = v.realization;
-  hot.slot0 = slot0;
-  hot.nb_items = nb * IPW;
-  hot.np = np;
-  hot.err = err;
-  hot.desc = udesc;
-  hot.order = order;
-  hot.pc = pc;
-  hot.pcs = pcs;
-  hot.pgact = pgact;
 
   // Several exchange intervals per launch (fused exchange, ga.n_iv > 1): after each interval's
   // exchange step, taken by the last CTA to arrive, the other CTAs wait for its release of xdone
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
       const uint32_t sweep = sweep0 + (uint32_t)(iv * nsw + (h >> 1));
       const uint32_t tag = tag_word(kTagMetro, v.stage, (uint32_t)c);
       auto process = [&](int i0, int i1) {
-        grid_process<L, BIM, GG, GTI>(hot, i0, i1, c, sweep, tag);
+        grid_process<L, BIM, GG, GTI>(&hot, i0, i1, c, sweep, tag);
       };
       // end planes (and the interior items sharing their rounds), then the progress word: the CTA
       // barrier orders every thread's end-plane stores before thread 0's gpu-scope fence and release
