@@ -40,9 +40,10 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 32 of them per SM per clock on GB300 (measured), which bounds the sweep at 6.4 attempts/clk/SM.
 MULWIDE_PER_CLK_SM = 32.0
 MULWIDE_PER_ATTEMPT = 5.0
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of each layout
-# (one exchange interval, 3.36e8 attempts, in either layout) from
-# one ncu capture of the current kernel version; None when the kernel changed since the capture.
+# dram__bytes_read.sum + dram__bytes_write.sum of a launch of one exchange interval (3.36e8
+# attempts) of the dominant kernel of each plan and layout, from one ncu capture of the current
+# kernel version; None when the kernel changed since the capture.  (The grid-wide plan runs up to
+# 64 intervals per launch in the timed steps; per interval it moves no more than this.)
 SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.724096e6,
                        "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6}
 
@@ -611,7 +612,8 @@ def roofline_of(m, layout, rf, props, steps):
     else:
         kernel = "k_sweeps_grid" if m.get("plan", "").startswith("0,") else "k_sweeps_bits"
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s", "frac": achieved / peak,
-            "traffic": SWEEP_TRAFFIC_BYTES.get(kernel), "traffic_unit": "bytes per launch (DRAM read+write, ncu)",
+            "traffic": SWEEP_TRAFFIC_BYTES.get(kernel),
+            "traffic_unit": "bytes per exchange interval (ncu, DRAM read+write of a one-interval launch)",
             "kernel": kernel, "plan": m.get("plan"),
             "peak_basis": f"Philox4x32-10 IMAD.WIDE limit: {MULWIDE_PER_CLK_SM:.0f}/clk/SM (measured) / "
                           f"{MULWIDE_PER_ATTEMPT:.0f} per attempt x {props.multi_processor_count} SMs x "
