@@ -309,8 +309,8 @@ int rfim_exchange_noalloc(const rfim_exchange_buffers *b, uint32_t j, int64_t me
    sweep-kernel launch group (one rfim_sweep / exchange-interval worth of sweeps) and every
    energy + exchange pair with CUDA events on the context's stream; rfim_profile(ctx, 0) stops.
    rfim_profile_read synchronises the stream and returns the summed device time (ms) and the
-   number of bracketed groups of each kind since the last rfim_profile call.  Any output pointer
-   may be NULL. */
+   number of bracketed groups of each kind since the last rfim_profile call (a grid-wide launch
+   that runs k exchange intervals counts k sweep groups).  Any output pointer may be NULL. */
 int rfim_profile(rfim_ctx *ctx, int enable);
 int rfim_profile_read(rfim_ctx *ctx, double *sweep_ms, int64_t *sweep_launches, double *exchange_ms,
                       int64_t *exchange_launches);
