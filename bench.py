@@ -45,7 +45,8 @@ MULWIDE_PER_ATTEMPT = 5.0
 # kernel version; None when the kernel changed since the capture.  (The grid-wide plan runs up to
 # 64 intervals per launch in the timed steps; per interval it moves no more than this.)
 SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.724096e6,
-                       "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6}
+                       "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6,
+                       "k_sweeps_grid (int8 layout staged as bits)": None}
 
 
 def parse():
@@ -605,12 +606,11 @@ def roofline_of(m, layout, rf, props, steps):
     achieved = L ** 3 * R * EX / (group_ms * 1e6)  # Gattempts/s
     sm_mhz = clk["sm_mhz"] or 2070.0
     peak = MULWIDE_PER_CLK_SM / MULWIDE_PER_ATTEMPT * props.multi_processor_count * sm_mhz * 1e-3
-    # the int8 layout at L = 64 runs the cluster kernel with its slabs staged from bytes into bits;
-    # the bit layout runs the grid-wide kernel when its plan says S = 0
+    # the int8 layout at L = 64 runs the same kernels with the lattice staged from bytes into bits;
+    # the grid-wide kernel when the plan says S = 0
+    kernel = "k_sweeps_grid" if m.get("plan", "").startswith("0,") else "k_sweeps_bits"
     if layout != rf.LAYOUT_BITPACK:
-        kernel = "k_sweeps_bits (int8 layout staged as bits)"
-    else:
-        kernel = "k_sweeps_grid" if m.get("plan", "").startswith("0,") else "k_sweeps_bits"
+        kernel += " (int8 layout staged as bits)"
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gattempts/s", "frac": achieved / peak,
             "traffic": SWEEP_TRAFFIC_BYTES.get(kernel),
             "traffic_unit": "bytes per exchange interval (ncu, DRAM read+write of a one-interval launch)",

@@ -91,15 +91,17 @@ int words_per_cta(int L, int S) { return L <= 0 || S <= 0 ? 0 : (L / S) * (L * L
 
 using GridFn = void (*)(RealView, GridArgs, uint32_t, int32_t, const float4 *, ExchArgs);
 
-template <int L, int GG, int GTI, int NT>
+template <int L, int GG, int GTI, int NT, bool I8 = false>
 GridFn grid_pick(bool bim) {
-  return bim ? (GridFn)k_sweeps_grid<L, true, GG, GTI, NT> : (GridFn)k_sweeps_grid<L, false, GG, GTI, NT>;
+  return bim ? (GridFn)k_sweeps_grid<L, true, GG, GTI, NT, I8> : (GridFn)k_sweeps_grid<L, false, GG, GTI, NT, I8>;
 }
 
 // Grid-wide instances: G replicas per unit, GT of them per thread item (GT = G: one field load
 // per group); NT is the launch-bounds thread count (plans may launch fewer threads, in multiples
 // of 32).
-GridFn grid_kernel_for(int L, int G, int GT, int threads, bool bim) {
+GridFn grid_kernel_for(int L, int G, int GT, int threads, bool bim, bool i8) {
+  if (i8)  // the int8 layout staged as bits: the default shape only
+    return L == 64 && G == 4 && GT == 4 && threads > 256 && threads <= 512 ? grid_pick<64, 4, 4, 512, true>(bim) : nullptr;
   if (threads <= 512) {
     if (L == 64 && G == 4 && GT == 4) return grid_pick<64, 4, 4, 512>(bim);
     if (L == 64 && G == 4 && GT == 1) return grid_pick<64, 4, 1, 512>(bim);
@@ -263,9 +265,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   p.i8 = i8;
   int sms_dev = 0;
   cudaDeviceGetAttribute(&sms_dev, cudaDevAttrMultiProcessorCount, 0);
-  if (L == 64 && i8) {
-    p.S = 4; p.G = 4; p.GT = 4; p.threads = 512;  // int8 staging: the cluster shape only
-  } else if (L == 64) {
+  if (L == 64) {  // both layouts (the int8 one staged as bits)
     // clusters of 4 z slabs x 4 replicas, unless they would leave more than a fifth of the SMs
     // idle (e.g. R = 70 after adaptation: 72 CTAs) or need more clusters than fit at once (a
     // second wave; 36 clusters of 4 at one CTA per SM on GB300); then the grid-wide plan
@@ -329,8 +329,8 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     const int nf = sscanf(o, "%d,%d,%d,%d,%d", &s, &g, &gt, &th, &ns);
     const bool named = nf == 4 || nf == 5;
     if (nf == 4) ns = 1;
-    const bool exists = named && (s == 0 ? (!i8 && ns == 1 && th >= 256 && th <= 1024 && th % 32 == 0 &&
-                                            grid_kernel_for(L, g, gt, th, bimodal))
+    const bool exists = named && (s == 0 ? (ns == 1 && th >= 256 && th <= 1024 && th % 32 == 0 &&
+                                            grid_kernel_for(L, g, gt, th, bimodal, i8))
                                          : kernel_for(L, s, gt, th, bimodal, i8, ns) != nullptr);
     if (exists) {
       p.S = s; p.G = g; p.GT = gt; p.threads = th; p.NS = ns;
@@ -344,7 +344,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   KernelFn fn = p.S == 0 ? nullptr : kernel_for(L, p.S, p.GT, p.threads, bimodal, i8, p.NS);
-  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.G, p.GT, p.threads, bimodal) : nullptr;
+  GridFn gfn = p.S == 0 && p.threads >= 256 && p.threads <= 1024 ? grid_kernel_for(L, p.G, p.GT, p.threads, bimodal, i8) : nullptr;
   if (!fn && !gfn) {
     if (err) *err = "no bit-layout kernel instance for this plan";
     return -1;  // RFIM_EINVAL
@@ -407,6 +407,8 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
     if (!rc) rc = grab((void **)&p.gpartFi, gslots * 8, "grid partials");
     if (!rc) rc = grab((void **)&p.gpartF, gslots * 8, "grid partials");
     if (!rc) rc = grab((void **)&p.prog, (size_t)std::max(sms, 1) * 4, "progress words");
+    // int8 layout: the published end planes (halos) in the bit layout
+    if (!rc && i8) rc = grab((void **)&p.gbits, (size_t)Rcap * 2 * ((size_t)L * L * L / 64) * 4, "halo words");
   }
   if (!rc && cudaMemset(p.counter, 0, 16) != cudaSuccess) rc = -3;
   if (!rc && p.prog && cudaMemset(p.prog, 0, (size_t)std::max(sms, 1) * 4) != cudaSuccess) rc = -3;
@@ -422,7 +424,7 @@ bool bits_plan_fits(const BitsPlan &plan, int32_t R) { return R <= plan.Rcap; }
 
 void free_bits_plan(BitsPlan &plan) {
   void *ptrs[] = {plan.field4, plan.flimb, plan.fquant, plan.partB, plan.partM, plan.partFi, plan.partF,
-                  plan.counter, plan.gpartB, plan.gpartM, plan.gpartFi, plan.gpartF, plan.prog};
+                  plan.counter, plan.gpartB, plan.gpartM, plan.gpartFi, plan.gpartF, plan.prog, plan.gbits};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   plan.field4 = nullptr;
@@ -434,6 +436,7 @@ void free_bits_plan(BitsPlan &plan) {
   plan.gpartB = plan.gpartM = plan.gpartFi = nullptr;
   plan.gpartF = nullptr;
   plan.prog = nullptr;
+  plan.gbits = nullptr;
 }
 
 cudaError_t build_field4(const RealView &v, BitsPlan &plan, cudaStream_t st) {
@@ -469,8 +472,10 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
   xa.flimb = plan.flimb;
   xa.fquant = plan.fquant;
   if (plan.S == 0) {
-    GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal);
-    if (!gfn) return cudaErrorInvalidConfiguration;
+    GridFn gfn = grid_kernel_for(plan.L, plan.G, plan.GT, plan.threads, v.kind == kBimodal, plan.i8);
+    if (!gfn || (plan.i8 && !plan.gbits)) return cudaErrorInvalidConfiguration;
+    RealView vg = v;
+    if (plan.i8) vg.bits = plan.gbits;  // halos go through the bit-layout scratch
     if (n_intervals < 1) return cudaErrorInvalidValue;
     GridArgs ga = grid_args(plan, v.R, plan.sms);
     const uint32_t niv = (uint32_t)(exchange ? n_intervals : 1);
@@ -500,7 +505,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, gfn, v, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, gfn, vg, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
     if (le != cudaSuccess) {  // nothing ran: the words did not advance
       plan.prog_base -= add;
       plan.x_base -= niv;

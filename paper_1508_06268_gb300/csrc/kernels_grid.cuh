@@ -143,7 +143,10 @@ __device__ __noinline__ void grid_process(const GridHot *hot_s, int i0, int i1, 
   }
 }
 
-template <int L, bool BIM, int GG, int GTI, int NT>
+// I8: the realization lives in the int8 layout (v.spins8); the CTA packs its pieces and the first
+// halos from bytes and unpacks its pieces at the end, and v.bits is a scratch array in the bit
+// layout that carries only the end planes published during the launch.
+template <int L, bool BIM, int GG, int GTI, int NT, bool I8 = false>
 __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, uint32_t sweep0, int32_t nsw,
                                                         const float4 *__restrict__ field4, ExchArgs xa) {
   constexpr int PW = L * L / 64, W = L * L * L / 64;
@@ -201,7 +204,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     const uint32_t d = udesc[lu];
     const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
     const int r = pc[p].g * GG + gg, z = pc[p].z0 + zl;
-    at(p, gg, c, zl)[w] = r < v.R ? v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] : 0u;
+    const int64_t gw = ((int64_t)r * 2 + c) * W + (int64_t)z * PW + w;
+    at(p, gg, c, zl)[w] = r < v.R ? (I8 ? pack_int8_word(v.spins8 + 32 * gw) : v.bits[gw]) : 0u;
   }
   tab_fill<BIM>(v, tab, slot0, np * GG, [&](int t) { return min(pc[t / GG].g * GG + t % GG, v.R - 1); });
   __syncthreads();
@@ -219,7 +223,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   // their CTAs have published `need` half-sweeps: thread `lead` waits, the group of `count`
   // threads (whole warps, named barrier `bar`) holding it then loads.  The caller makes the loads
   // visible with a CTA barrier.
-  auto fetch_halos = [&](int other, unsigned need, int t0, int count, int bar) {
+  // from_bytes: the int8 layout as the launch found it (the first halos of an I8 launch)
+  auto fetch_halos = [&](int other, unsigned need, int t0, int count, int bar, bool from_bytes = false) {
     const int lt = tid - t0;
     if (lt == 0) {
       for (int p = 0; p < np; ++p) {
@@ -236,11 +241,12 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
       const int p = t / (2 * GG * PW), side = (t / (GG * PW)) & 1, gg = (t / PW) % GG, w = t % PW;
       const int r = min(pc[p].g * GG + gg, v.R - 1);
       const int z = side ? (pc[p].z0 + pc[p].n) % L : (pc[p].z0 + L - 1) % L;
-      at(p, gg, other, side ? pc[p].n : -1)[w] = __ldcg(v.bits + ((int64_t)r * 2 + other) * W + (int64_t)z * PW + w);
+      const int64_t gw = ((int64_t)r * 2 + other) * W + (int64_t)z * PW + w;
+      at(p, gg, other, side ? pc[p].n : -1)[w] = from_bytes ? pack_int8_word(v.spins8 + 32 * gw) : __ldcg(v.bits + gw);
     }
   };
   // the neighbours' colour-1 end planes as the launch found them
-  fetch_halos(1, ga.prog_base, 0, nt, 1);
+  fetch_halos(1, ga.prog_base, 0, nt, 1, I8);
   __shared__ GridHot hot;
   if (tid == 0) {
     hot.lat = lat;
@@ -305,7 +311,13 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
         const uint32_t d = udesc[lu];
         const int p = (int)(d >> 26), zl = (int)((d >> 18) & 255u);
         const int r = pc[p].g * GG + gg, z = pc[p].z0 + zl;
-        if (r < v.R) v.bits[((int64_t)r * 2 + c) * W + (int64_t)z * PW + w] = at(p, gg, c, zl)[w];
+        const int64_t gw = ((int64_t)r * 2 + c) * W + (int64_t)z * PW + w;
+        if (r < v.R) {
+          if (I8)
+            unpack_int8_word(at(p, gg, c, zl)[w], v.spins8 + 32 * gw);
+          else
+            v.bits[gw] = at(p, gg, c, zl)[w];
+        }
       }
     }
     if (!xa.enabled) return;

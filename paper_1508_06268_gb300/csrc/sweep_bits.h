@@ -32,6 +32,7 @@ struct BitsPlan {
   long long *gpartB = nullptr, *gpartM = nullptr, *gpartFi = nullptr;
   double *gpartF = nullptr;
   unsigned int *prog = nullptr;
+  uint32_t *gbits = nullptr;  // int8 layout on the grid-wide plan: published end planes as bits
   // progress count the grid-wide kernel's words held when the next launch starts (each launch
   // adds its half-sweeps, so no launch has to zero them first)
   mutable uint32_t prog_base = 0;

@@ -429,6 +429,21 @@ def test_grid_wide_variant_bit_exact(L, R, plan, monkeypatch):
     np.testing.assert_array_equal(g.observables()["sums"], o.observables())
 
 
+@pytest.mark.parametrize("R", [6, 70, 128])
+def test_grid_wide_int8_layout_bit_exact(R):
+    """The int8 layout on the grid-wide plan (pieces and first halos packed from the bytes, halos
+    published as bits in a scratch array during the launch, pieces unpacked at its end), several
+    intervals per launch, against the oracle: bimodal field, spins, permutation and sums exact."""
+    temps = inputs.geometric_temps(1.0, 5.0, R)
+    g, o = make_pair(64, temps, kind=BIM, layout=I8, h=1.5, field_seed=3, seed=42)
+    assert g.plan() == "0,4,4,512,int8"
+    g.run(6, 3, 0)
+    o.run(6, 3, 0)
+    assert_same_state(g, o, "int8 grid plan")
+    np.testing.assert_array_equal(g.observables()["sums"], o.observables())
+    g.close()
+
+
 @pytest.mark.parametrize("kind", [BIM, EXP])
 def test_grid_wide_many_intervals_per_launch(kind, monkeypatch):
     """The grid-wide plan runs up to 64 exchange intervals per launch (the last CTA's exchange step
