@@ -46,7 +46,7 @@ MULWIDE_PER_ATTEMPT = 5.0
 # 64 intervals per launch in the timed steps; per interval it moves no more than this.)
 SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.724096e6,
                        "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6,
-                       "k_sweeps_grid (int8 layout staged as bits)": None}
+                       "k_sweeps_grid (int8 layout staged as bits)": 36.1344e6}
 
 
 def parse():
