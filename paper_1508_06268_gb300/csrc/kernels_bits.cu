@@ -138,6 +138,7 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
   ga.n_iv = 1;
   ga.x_base = 0;
   ga.xdone = p.counter ? p.counter + 2 : nullptr;
+  ga.rcap = p.Rcap;
   ga.partB = p.gpartB;
   ga.partM = p.gpartM;
   ga.partFi = p.gpartFi;
@@ -145,10 +146,12 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
   return ga;
 }
 
-size_t grid_smem(int L, int G, int max_units) {
+size_t grid_smem(int L, int G, int max_units, int rcap) {
   const size_t PW = (size_t)L * L / 64;
-  // piece regions with two halo planes each (both colours), then the decision-table slots
-  const size_t need = (size_t)(max_units + 2 * kGridMaxPieces) * G * 2 * PW * 4 + tab_bytes(kGridMaxPieces * G);
+  // piece regions with two halo planes each (both colours), the decision-table slots, then the
+  // exchange state every CTA keeps (grid_xs_bytes)
+  const size_t need = (size_t)(max_units + 2 * kGridMaxPieces) * G * 2 * PW * 4 + tab_bytes(kGridMaxPieces * G) +
+                      grid_xs_bytes(rcap);
   return std::max(need, kGridMinSmem);
 }
 
@@ -361,7 +364,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
       if (err) *err = "grid plan: too many planes per CTA";
       return -1;
     }
-    p.smem = grid_smem(L, p.G, maxu);
+    p.smem = grid_smem(L, p.G, maxu, Rcap);
   }
   if (!gfn)
     p.smem = (size_t)p.G * 2 * words_per_cta(L, p.S) * 4 + tab_bytes(p.G);
@@ -401,7 +404,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!rc) rc = grab((void **)&p.partF, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.counter, 16, "counter");  // arrivals, error word, exchange steps done
   if (!rc && gfn) {
-    const size_t gslots = (size_t)Rcap * (L + 1);
+    const size_t gslots = 2 * (size_t)Rcap * (L + 1);  // two intervals' partials
     rc = grab((void **)&p.gpartB, gslots * 8, "grid partials");
     if (!rc) rc = grab((void **)&p.gpartM, gslots * 8, "grid partials");
     if (!rc) rc = grab((void **)&p.gpartFi, gslots * 8, "grid partials");
@@ -480,12 +483,13 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     GridArgs ga = grid_args(plan, v.R, plan.sms);
     const uint32_t niv = (uint32_t)(exchange ? n_intervals : 1);
     const uint32_t add = 2u * (uint32_t)n_sweeps * niv;
+    const uint32_t arrivals = exchange ? (uint32_t)ga.gp.P * niv : 0u;  // one per CTA and interval
     if (plan.prog_base > 0xFFFFFFFFu - add) {  // the count would wrap: start again from zero
       const cudaError_t e = cudaMemsetAsync(plan.prog, 0, (size_t)plan.sms * 4, st);
       if (e != cudaSuccess) return e;
       plan.prog_base = 0;
     }
-    if (plan.x_base > 0xFFFFFFFFu - niv) {
+    if (plan.x_base > 0xFFFFFFFFu - arrivals) {
       const cudaError_t e = cudaMemsetAsync(plan.counter + 2, 0, 4, st);
       if (e != cudaSuccess) return e;
       plan.x_base = 0;
@@ -494,7 +498,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     ga.n_iv = (int32_t)niv;
     ga.x_base = plan.x_base;
     plan.prog_base += add;
-    plan.x_base += niv;
+    plan.x_base += arrivals;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ga.gp.P);
     cfg.blockDim = dim3((unsigned)plan.threads);
@@ -508,7 +512,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     const cudaError_t le = cudaLaunchKernelEx(&cfg, gfn, vg, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
     if (le != cudaSuccess) {  // nothing ran: the words did not advance
       plan.prog_base -= add;
-      plan.x_base -= niv;
+      plan.x_base -= arrivals;
     }
     return le;
   }

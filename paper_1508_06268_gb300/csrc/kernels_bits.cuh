@@ -164,16 +164,15 @@ __device__ __forceinline__ uint32_t tab_slot0(const void *p) {
   return ((uint32_t)__cvta_generic_to_shared(p) + kTabSlot - 1u) & ~(kTabSlot - 1u);
 }
 
-// Fills the tables of n replicas, slot g for replica replica_of(g), with all threads of the CTA.
+// Fills the tables of n slots, slot g for temperature temp_of(g), with all threads of the CTA.
 // `base` is any generic pointer into dynamic shared memory at or before the slots.
-// CG: read the temperature assignment through L2 (another CTA of the launch changed it).
-template <bool BIM, bool CG = false, class F>
-__device__ __forceinline__ void tab_fill(const RealView &v, void *base, uint32_t slot0, int n, F replica_of) {
+template <bool BIM, class F>
+__device__ __forceinline__ void tab_fill_temps(const RealView &v, void *base, uint32_t slot0, int n, F temp_of) {
   constexpr int E = BIM ? 32 : 16;
   char *gen = reinterpret_cast<char *>(base) + (slot0 - (uint32_t)__cvta_generic_to_shared(base));
   for (int t = threadIdx.x; t < n * E; t += blockDim.x) {
     const int g = t / E, i = t % E;
-    const int k = CG ? __ldcg(v.r2t + replica_of(g)) : v.r2t[replica_of(g)];
+    const int k = temp_of(g);
     char *slot = gen + (size_t)g * kTabSlot;
     if (BIM) {
       reinterpret_cast<uint32_t *>(slot)[i] = v.thr[(int64_t)k * 32 + i];
@@ -182,6 +181,12 @@ __device__ __forceinline__ void tab_fill(const RealView &v, void *base, uint32_t
       reinterpret_cast<float2 *>(slot)[i] = make_float2(__fmul_rn(b, v.gjn[i & 7]), b);
     }
   }
+}
+
+// The same with slot g for the temperature of replica replica_of(g).
+template <bool BIM, class F>
+__device__ __forceinline__ void tab_fill(const RealView &v, void *base, uint32_t slot0, int n, F replica_of) {
+  tab_fill_temps<BIM>(v, base, slot0, n, [&](int g) { return v.r2t[replica_of(g)]; });
 }
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {

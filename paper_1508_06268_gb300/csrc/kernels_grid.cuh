@@ -27,16 +27,21 @@ struct GridArgs {
   GridPart gp;
   unsigned int *prog;  // [P] prog_base + half-sweeps completed by each CTA in this launch
   uint32_t prog_base;  // every word's value when the launch starts
-  // exchange intervals in this launch (with the fused exchange); between them the other CTAs wait
-  // for the last one's release of *xdone = x_base + interval + 1
+  // exchange intervals in this launch (with the fused exchange); after each interval's partials
+  // every CTA adds one to *xdone and waits for x_base + P (interval + 1) arrivals
   int32_t n_iv;
   uint32_t x_base;
   unsigned int *xdone;
+  int32_t rcap;  // replica capacity: partials are [2 intervals][rcap][slots]
   int32_t max_units;   // units of the largest CTA (shared-memory sizing)
   int32_t slots;       // partial-sum slots per replica (CTAs sharing one group, at most)
   long long *partB, *partM, *partFi;  // [Rcap][slots]
   double *partF;
 };
+
+// Shared-memory exchange state every CTA of the grid-wide kernel keeps: t2r, r2t (int32), E
+// (double), M (int64) for rcap replicas, 8-byte aligned.
+__host__ __device__ constexpr size_t grid_xs_bytes(int rcap) { return (size_t)rcap * 24 + 16; }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   unsigned v;
@@ -196,6 +201,18 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   uint32_t *lat = sm;                                                   // piece regions
   uint32_t *tab = lat + (size_t)(ga.max_units + 2 * kGridMaxPieces) * GG * 2 * PW;  // [pieces][GG] table slots
   const uint32_t slot0 = tab_slot0(tab);
+  // exchange state, after the table slots (tab_bytes includes the slots' alignment slack)
+  char *xs = reinterpret_cast<char *>(tab) + tab_bytes(kGridMaxPieces * GG);
+  xs += (8u - ((uintptr_t)xs & 7u)) & 7u;
+  double *E_s = reinterpret_cast<double *>(xs);
+  long long *M_s = reinterpret_cast<long long *>(E_s + ga.rcap);
+  int32_t *t2r_s = reinterpret_cast<int32_t *>(M_s + ga.rcap);
+  int32_t *r2t_s = t2r_s + ga.rcap;
+  if (xa.enabled)
+    for (int r = tid; r < v.R; r += nt) {
+      t2r_s[r] = v.t2r[r];
+      r2t_s[r] = v.r2t[r];
+    }
   // word w of plane zl (-1 .. n_p: halos included) of colour c of replica gg in piece p
   auto at = [&](int p, int gg, int c, int zl) { return lat + pbase[p] + (gg * 2 + c) * pcs[p] + (zl + 1) * PW; };
 
@@ -274,7 +291,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   for (int iv = 0; iv < n_iv; ++iv) {
     const unsigned pbase = ga.prog_base + (unsigned)(2 * nsw * iv);
     if (iv > 0) {
-      tab_fill<BIM, true>(v, tab, slot0, np * GG, [&](int t) { return min(pc[t / GG].g * GG + t % GG, v.R - 1); });
+      // tables of the temperatures the previous exchange step assigned
+      tab_fill_temps<BIM>(v, tab, slot0, np * GG, [&](int t) { return r2t_s[min(pc[t / GG].g * GG + t % GG, v.R - 1)]; });
       __syncthreads();
     }
     for (int h = 0; h < 2 * nsw; ++h) {
@@ -332,7 +350,6 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     __shared__ int red_i[BIM ? 3 : 2][RB][32];
     __shared__ long long red_l[BIM ? 1 : RB][32];
     __shared__ double red_d[RB][32];
-    __shared__ int last_cta;
     const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
     const bool limbs = !BIM && xa.flimb != nullptr;
     for (int p = 0; p < np; ++p) {
@@ -442,7 +459,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
           if (lane == 0) {
             const int slab = grid_slab_of(ga.gp, k, pc[p].g);
             const int r = pc[p].g * GG + g0 + gg;
-            const int64_t slot = (int64_t)r * ga.slots + slab;
+            const int64_t slot = ((int64_t)(iv & 1) * ga.rcap + r) * ga.slots + slab;
             if (RFIM_DCHECK(xa.err, slab >= 0 && slab < ga.slots && r < v.R, kDbgPartition)) {
               ga.partB[slot] = tb;
               ga.partM[slot] = tm;
@@ -454,44 +471,71 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
         __syncthreads();
       }
     }
+    // Every CTA takes exchange step j + iv itself: after all P CTAs have arrived with their
+    // partials, each sums every replica's energy (Eq. 1) in the same order and takes the same
+    // decisions on its own copy of the temperature assignment; CTA 0 alone keeps the global state
+    // (counts, measurement, and the assignment and energies after the launch's last step).  The
+    // partials alternate between two buffers, so a CTA already in the next interval does not
+    // overwrite sums that a slower one is still reading.
     if (tid == 0) {
       __threadfence();
-      last_cta = atomicAdd(xa.counter, 1u) == gridDim.x - 1;
+      atomicAdd(ga.xdone, 1u);
+      grid_wait(ga.xdone, 0, ga.x_base + (unsigned)gridDim.x * (unsigned)(iv + 1), err);
     }
     __syncthreads();
-    if (last_cta) {
-      __threadfence();
-      for (int r = tid; r < v.R; r += nt) {
-        const int g = r / GG;
-        const int nslab = grid_owner(ga.gp, (int64_t)g * L + L - 1) - grid_owner(ga.gp, (int64_t)g * L) + 1;
-        long long tb = 0, tm = 0, tf = 0;
-        double td = 0.0;
-        for (int q = 0; q < nslab; ++q) {
-          const int64_t slot = (int64_t)r * ga.slots + q;
-          tb += __ldcg(ga.partB + slot);
-          tm += __ldcg(ga.partM + slot);
-          tf += __ldcg(ga.partFi + slot);
-          td += __ldcg(ga.partF + slot);
-        }
-        const double F = BIM ? xa.h * (double)tf
-                             : (xa.flimb ? ldexp((double)(2 * tf - xa.fquant->Htot), xa.fquant->qe) : td);
-        v.E[r] = -xa.J * (double)tb - F;
-        v.M[r] = tm;
+    const uint32_t jx = xa.j + (uint32_t)iv;
+    const int64_t pb = (int64_t)(iv & 1) * ga.rcap;
+    for (int r = tid; r < v.R; r += nt) {
+      const int g = r / GG;
+      const int nslab = grid_owner(ga.gp, (int64_t)g * L + L - 1) - grid_owner(ga.gp, (int64_t)g * L) + 1;
+      long long tb = 0, tm = 0, tf = 0;
+      double td = 0.0;
+      for (int q = 0; q < nslab; ++q) {
+        const int64_t slot = (pb + r) * ga.slots + q;
+        tb += __ldcg(ga.partB + slot);
+        tm += __ldcg(ga.partM + slot);
+        tf += __ldcg(ga.partFi + slot);
+        td += __ldcg(ga.partF + slot);
       }
-      __syncthreads();
-      if (n_iv > 1)
-        exchange_and_measure<true>(v, xa.j + (uint32_t)iv, xa.measure_from);
-      else
-        exchange_and_measure(v, xa.j, xa.measure_from);
-      if (tid == 0) {
-        *xa.counter = 0u;
-        if (iv + 1 < n_iv) {
-          __threadfence();
-          st_release_u32(ga.xdone, ga.x_base + (unsigned)(iv + 1));
-        }
+      const double F = BIM ? xa.h * (double)tf
+                           : (xa.flimb ? ldexp((double)(2 * tf - xa.fquant->Htot), xa.fquant->qe) : td);
+      E_s[r] = -xa.J * (double)tb - F;
+      M_s[r] = tm;
+    }
+    __syncthreads();
+    for (int pr = tid;; pr += nt) {
+      const int32_t kk = (int32_t)(jx & 1u) + 2 * pr;
+      if (kk + 1 >= v.R) break;
+      const int32_t a = t2r_s[kk], b = t2r_s[kk + 1];
+      const bool accept = exchange_accept(v, jx, kk, E_s[a], E_s[b]);
+      if (k == 0) {
+        v.att[kk] += 1;
+        if (accept) v.acc[kk] += 1;
       }
-    } else if (iv + 1 < n_iv && tid == 0) {
-      grid_wait(ga.xdone, 0, ga.x_base + (unsigned)(iv + 1), err);
+      if (accept) {
+        t2r_s[kk] = b;
+        t2r_s[kk + 1] = a;
+        r2t_s[b] = kk;
+        r2t_s[a] = kk + 1;
+      }
+    }
+    __syncthreads();
+    if (k == 0) {
+      if ((int64_t)jx >= xa.measure_from) {
+        const double Nd = (double)v.N;
+        for (int kk = tid; kk < v.R; kk += nt) {
+          const int32_t a = t2r_s[kk];
+          measure_add(v.obs + (int64_t)kk * 5, E_s[a], M_s[a], Nd);
+        }
+        if (tid == 0) *v.n_meas += 1;
+      }
+      if (iv == n_iv - 1)
+        for (int r = tid; r < v.R; r += nt) {
+          v.t2r[r] = t2r_s[r];
+          v.r2t[r] = r2t_s[r];
+          v.E[r] = E_s[r];
+          v.M[r] = M_s[r];
+        }
     }
     __syncthreads();
   }  // exchange intervals
