@@ -44,9 +44,9 @@ MULWIDE_PER_ATTEMPT = 5.0
 # attempts) of the dominant kernel of each plan and layout, from one ncu capture of the current
 # kernel version; None when the kernel changed since the capture.  (The grid-wide plan runs up to
 # 64 intervals per launch in the timed steps; per interval it moves no more than this.)
-SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.724096e6,
+SWEEP_TRAFFIC_BYTES = {"k_sweeps_bits": 6.654976e6, "k_sweeps_grid": 6.723328e6,
                        "k_sweeps_bits (int8 layout staged as bits)": 36.020992e6,
-                       "k_sweeps_grid (int8 layout staged as bits)": 36.1344e6}
+                       "k_sweeps_grid (int8 layout staged as bits)": 36.098304e6}
 
 
 def parse():
