@@ -11,8 +11,11 @@
 // the global lattice as they are done and releases the CTA's progress word; the interior planes
 // follow.  During the last round, warps without an item acquire the neighbours' progress words
 // and load their end planes (L2) for the next half-sweep, so the neighbours have normally
-// published long before they are needed.  Waits are bounded (expiry sets the kernel's error word
-// and every later wait returns at once); the kernel always terminates.
+// published long before they are needed.  With the fused exchange a launch runs up to n_iv
+// exchange intervals: after each interval's energy partials all CTAs meet at an arrival count,
+// and every CTA takes the exchange step on its own copy of the temperature assignment.  Waits are
+// bounded (expiry sets the kernel's error word and every later wait returns at once); the kernel
+// always terminates.
 #pragma once
 #include <cstdint>
 
@@ -284,9 +287,9 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
   }
   __syncthreads();
 
-  // Several exchange intervals per launch (fused exchange, ga.n_iv > 1): after each interval's
-  // exchange step, taken by the last CTA to arrive, the other CTAs wait for its release of xdone
-  // and refill their decision tables for the new temperature assignment.
+  // Several exchange intervals per launch (fused exchange, ga.n_iv > 1): every CTA takes each
+  // interval's exchange step itself (below) and refills its decision tables from its own copy of
+  // the new temperature assignment.
   const int n_iv = xa.enabled ? max(ga.n_iv, 1) : 1;
   for (int iv = 0; iv < n_iv; ++iv) {
     const unsigned pbase = ga.prog_base + (unsigned)(2 * nsw * iv);
