@@ -136,8 +136,8 @@ GridArgs grid_args(const BitsPlan &p, int32_t R, int sms) {
   ga.prog = p.prog;
   ga.prog_base = 0;
   ga.n_iv = 1;
-  ga.x_base = 0;
-  ga.xdone = p.counter ? p.counter + 2 : nullptr;
+  ga.arrive_base = 0;
+  ga.arrive = p.counter ? p.counter + 2 : nullptr;
   ga.rcap = p.Rcap;
   ga.partB = p.gpartB;
   ga.partM = p.gpartM;
@@ -489,16 +489,16 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
       if (e != cudaSuccess) return e;
       plan.prog_base = 0;
     }
-    if (plan.x_base > 0xFFFFFFFFu - arrivals) {
+    if (plan.arrive_base > 0xFFFFFFFFu - arrivals) {
       const cudaError_t e = cudaMemsetAsync(plan.counter + 2, 0, 4, st);
       if (e != cudaSuccess) return e;
-      plan.x_base = 0;
+      plan.arrive_base = 0;
     }
     ga.prog_base = plan.prog_base;
     ga.n_iv = (int32_t)niv;
-    ga.x_base = plan.x_base;
+    ga.arrive_base = plan.arrive_base;
     plan.prog_base += add;
-    plan.x_base += arrivals;
+    plan.arrive_base += arrivals;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ga.gp.P);
     cfg.blockDim = dim3((unsigned)plan.threads);
@@ -512,7 +512,7 @@ cudaError_t launch_sweeps_bits(const RealView &v, const BitsPlan &plan, uint32_t
     const cudaError_t le = cudaLaunchKernelEx(&cfg, gfn, vg, ga, sweep0, n_sweeps, (const float4 *)plan.field4, xa);
     if (le != cudaSuccess) {  // nothing ran: the words did not advance
       plan.prog_base -= add;
-      plan.x_base -= arrivals;
+      plan.arrive_base -= arrivals;
     }
     return le;
   }

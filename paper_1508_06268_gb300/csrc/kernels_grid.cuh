@@ -31,10 +31,10 @@ struct GridArgs {
   unsigned int *prog;  // [P] prog_base + half-sweeps completed by each CTA in this launch
   uint32_t prog_base;  // every word's value when the launch starts
   // exchange intervals in this launch (with the fused exchange); after each interval's partials
-  // every CTA adds one to *xdone and waits for x_base + P (interval + 1) arrivals
+  // every CTA adds one to *arrive and waits for arrive_base + P (interval + 1) arrivals
   int32_t n_iv;
-  uint32_t x_base;
-  unsigned int *xdone;
+  uint32_t arrive_base;
+  unsigned int *arrive;
   int32_t rcap;  // replica capacity: partials are [2 intervals][rcap][slots]
   int32_t max_units;   // units of the largest CTA (shared-memory sizing)
   int32_t slots;       // partial-sum slots per replica (CTAs sharing one group, at most)
@@ -482,8 +482,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweeps_grid(RealView v, GridArgs ga, 
     // overwrite sums that a slower one is still reading.
     if (tid == 0) {
       __threadfence();
-      atomicAdd(ga.xdone, 1u);
-      grid_wait(ga.xdone, 0, ga.x_base + (unsigned)gridDim.x * (unsigned)(iv + 1), err);
+      atomicAdd(ga.arrive, 1u);
+      grid_wait(ga.arrive, 0, ga.arrive_base + (unsigned)gridDim.x * (unsigned)(iv + 1), err);
     }
     __syncthreads();
     const uint32_t jx = xa.j + (uint32_t)iv;

@@ -211,7 +211,7 @@ int check_device_error(rfim_ctx *c) {
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.prog, 0, (size_t)std::max(c->plan.sms, 1) * 4, c->stream));
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->plan.counter + 2, 0, 4, c->stream));
     c->plan.prog_base = 0;
-    c->plan.x_base = 0;
+    c->plan.arrive_base = 0;
   }
   if (word & kDbgMask)
     return fail(c, RFIM_EBOUNDS, "a bounds check of the debug build failed (error word 0x%x); the checked accesses were skipped", word);

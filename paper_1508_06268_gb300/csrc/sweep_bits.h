@@ -36,7 +36,7 @@ struct BitsPlan {
   // progress count the grid-wide kernel's words held when the next launch starts (each launch
   // adds its half-sweeps, so no launch has to zero them first)
   mutable uint32_t prog_base = 0;
-  mutable uint32_t x_base = 0;  // the same for the exchange-step word (counter[2])
+  mutable uint32_t arrive_base = 0;  // the same for the arrival count of the exchange steps (counter[2])
   int32_t sms = 0;
   bool i8 = false;  // the realization is stored in the int8 layout and staged as bits (cluster shapes)
   int32_t NS = 1;   // 4: every word split over four warps, one block pair each (small lattices)
