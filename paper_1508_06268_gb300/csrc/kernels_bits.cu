@@ -402,7 +402,7 @@ int make_bits_plan(int32_t L, int32_t Rcap, bool bimodal, BitsPlan *plan, std::s
   if (!rc) rc = grab((void **)&p.partM, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partFi, parts * 8, "partials");
   if (!rc) rc = grab((void **)&p.partF, parts * 8, "partials");
-  if (!rc) rc = grab((void **)&p.counter, 16, "counter");  // arrivals, error word, exchange steps done
+  if (!rc) rc = grab((void **)&p.counter, 16, "counter");  // cluster arrivals, error word, grid-wide arrival count
   if (!rc && gfn) {
     const size_t gslots = 2 * (size_t)Rcap * (L + 1);  // two intervals' partials
     rc = grab((void **)&p.gpartB, gslots * 8, "grid partials");
