@@ -191,6 +191,12 @@ def cpu_baseline(budget_s=12.0):
     return out
 
 
+def c4_workload(args):
+    """The benchmarked workload, named the same way by both arms."""
+    return (f"C4: L=64 (262144 sites) Gaussian h=1, J=1, R=128 geometric [1,5], {args.sweeps} sweeps/step, "
+            f"exchange every {EX}")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -212,8 +218,8 @@ def run_reference(args):
         "unit": "attempts/ns", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64/f32 (oracle)", "data": "synthetic",
-        "config": {"workload": "C4: L=64 Gaussian h=1, R=128 geometric [1,5], exchange every 10",
-                   "sample": f"{per_step} sweeps per step"},
+        "config": {"workload": c4_workload(args), "layout": args.layout,
+                   "sample": f"each step {per_step} of its sweeps, on the host cores"},
         "cpu_baseline": {"value": value, "unit": "attempts/ns", "cores": 1, "kind": "oracle",
                          "sample": f"{per_step} sweeps of all 128 replicas per step"},
         "e2e": {"value": value, "unit": "attempts/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -691,8 +697,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": m["dev_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
-            "config": {"workload": "C4: L=64 (262144 sites) Gaussian h=1, J=1, R=128 geometric [1,5], "
-                                   f"{args.sweeps} sweeps/step, exchange every {EX}",
+            "config": {"workload": c4_workload(args),
                        "layout": args.layout, "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"realization per GPU x{world}",
                        "wall_s": m["wall"]},
